@@ -1,0 +1,151 @@
+/*
+ * tmfg.h -- C ABI of libtmfg.so: GB300 (sm_103a) TMFG construction and
+ * all-pairs shortest paths over the TMFG, after Raphael & Shun, "Faster
+ * Parallel Triangular Maximally Filtered Graphs and Hierarchical Clustering"
+ * (arXiv 2408.09399).
+ *
+ * Conventions for every entry point:
+ *  - Array arguments are DEVICE pointers owned by the caller (for example
+ *    torch tensors on the context's device).  The library never frees them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls are stream-ordered and asynchronous: they enqueue work
+ *    and return.
+ *  - The library allocates device memory only inside a tmfg_ctx (its
+ *    workspace), never more than the budget given to tmfg_create.  A context
+ *    may be used by one stream at a time.
+ *  - Argument errors are returned at once.  Errors found in the data (NaN,
+ *    |S| too large, asymmetry) are found on the device, recorded in the
+ *    context's status word, and returned by tmfg_sync_status.  Kernels that
+ *    run after a recorded error skip their work.
+ *  - No C++ exception crosses this interface; there is no CPU fallback.
+ *
+ * Matrix layout: S is n x n, row-major, with leading dimension ld >= n
+ * (elements), float (TMFG_F32) or double (TMFG_F64); the diagonal is never
+ * read for arithmetic; -0.0 and +0.0 are the same value.  Off-diagonal
+ * entries must be finite with |S| <= 64 (row sums are exact int64 sums of
+ * S*2^40).  Vertex ids are 0..n-1.
+ */
+#ifndef TMFG_H
+#define TMFG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+enum {
+    TMFG_OK = 0,
+    TMFG_EINVAL = 1,      /* bad argument (n < 4, ld < n, HEAP with prefix != 1, ...) */
+    TMFG_ENOMEM = 2,      /* workspace budget or device memory exhausted */
+    TMFG_ENONFINITE = 3,  /* S holds a NaN or an infinity off the diagonal */
+    TMFG_EASYMMETRIC = 4, /* S[i,j] != S[j,i] (only with TMFG_CHECK_SYMMETRY) */
+    TMFG_ETIMEOUT = 5,    /* a device loop reached its time limit and stopped */
+    TMFG_ECUDA = 6,       /* a CUDA runtime call failed */
+    TMFG_ERANGE = 7,      /* an off-diagonal |S| > 64 */
+    TMFG_ETOOBIG = 8,     /* n above what this build supports for the dtype */
+    TMFG_EINTERNAL = 9    /* an internal consistency check failed */
+};
+
+enum { TMFG_F32 = 0, TMFG_F64 = 1 };
+enum { TMFG_CORR = 0, TMFG_HEAP = 1 };
+
+/* tmfg_params.flags */
+#define TMFG_CHECK_SYMMETRY 1u /* verify S == S^T (bitwise, -0 == +0) first */
+
+typedef struct tmfg_ctx tmfg_ctx;
+
+/* Create a context on CUDA device `device` whose workspace may grow to
+ * `workspace_budget_bytes` (0 = no limit beyond free memory).  The context
+ * holds the device status word and the workspace.  Returns TMFG_OK and sets
+ * *out, or an error code (then *out is NULL). */
+int tmfg_create(tmfg_ctx **out, int device, size_t workspace_budget_bytes);
+
+/* Release the context's device memory.  Synchronises the device first. */
+void tmfg_destroy(tmfg_ctx *ctx);
+
+/* Largest n that tmfg_build supports for `dtype` in this build (the per-row
+ * sort keeps one row in shared memory). */
+int64_t tmfg_max_n(int dtype);
+
+/* Workspace bytes that tmfg_build (what = 0), tmfg_apsp exact (what = 1)
+ * or approximate (what = 2, with n_hubs = 0 meaning ceil(sqrt n)) needs. */
+size_t tmfg_workspace_bytes(int64_t n, int dtype, int what, int n_hubs);
+
+typedef struct {
+    int32_t mode;   /* TMFG_CORR (Algorithm 1) or TMFG_HEAP (Algorithm 2) */
+    int32_t prefix; /* prefix size P >= 1 for TMFG_CORR; must be 1 for TMFG_HEAP */
+    int32_t dtype;  /* TMFG_F32 or TMFG_F64: element type of S */
+    uint32_t flags; /* TMFG_CHECK_SYMMETRY or 0 */
+} tmfg_params;
+
+/* TMFG construction (Section 4.1, Algorithm 1 "corr-tmfg" and Section 4.2,
+ * Algorithm 2 "heap-tmfg"; lazily advanced sorted-row pointers of Section
+ * 4.3).  One up-front sort of every row of S, the initial 4-clique of the
+ * largest row sums, then n-4 greedy insertions of a vertex into a face.
+ *
+ * Outputs (device, int32, caller-owned):
+ *   order[n]            order[0..3] = the initial clique v1..v4 (row-sum
+ *                       rank order), order[4+k] = the k-th inserted vertex.
+ *   edges[(3n-6)*2]     the 6 clique edges (v1,v2),(v1,v3),(v1,v4),(v2,v3),
+ *                       (v2,v4),(v3,v4), then (v,x),(v,y),(v,z) for each
+ *                       insertion of v into face x<y<z.
+ *   ins_face[(n-4)*3]   the face x<y<z used by each insertion.
+ *   bubble_parent[n-3]  bubble tree: bubble 0 is the clique (parent -1);
+ *                       bubble k>=1 is insertion k-1; its parent is the
+ *                       bubble that created the face it used.
+ * Ties: a face's best vertex is the candidate of largest gain, then smallest
+ * id; pairs rank by (gain desc, vertex asc, face id asc).  The result is
+ * deterministic and does not depend on the GPU or the launch. */
+int tmfg_build(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, const tmfg_params *params,
+               int32_t *order, int32_t *edges, int32_t *ins_face, int32_t *bubble_parent,
+               void *stream);
+
+/* The per-row sort step alone (Algorithm 1, sort loop), for inspection and
+ * tests: idx[v*ldi + j] (uint16, ldi >= n-1) = the j-th vertex of row v
+ * sorted by (S[v,u] desc, u asc) over u != v; rowsum[v] (int64, may be
+ * NULL) = sum over u != v of S[v,u]*2^40 rounded to nearest-even.  n must be
+ * <= tmfg_max_n(dtype). */
+int tmfg_row_sort(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, int32_t dtype,
+                  uint16_t *idx, int64_t ldi, int64_t *rowsum, void *stream);
+
+typedef struct {
+    int32_t approx;      /* 0: exact APSP; 1: hub-based approximate APSP */
+    int32_t n_hubs;      /* approximate only; 0 = ceil(sqrt(n)) */
+    float radius_factor; /* approximate only; 0 = 2.0 */
+} tmfg_apsp_params;
+
+/* All-pairs shortest paths over the TMFG (Section 2: the distances DBHT
+ * uses; approximate form of Section 4.3).  Edge (a,b) of `edges` (3n-6 of
+ * them, as written by tmfg_build) has length sqrt(max(0, 2(1 - S[a,b])))
+ * computed in the dtype of S and rounded to float.  D[s*ldd + t] (float,
+ * ldd >= n) = the smallest left-to-right float sum of the lengths along a
+ * path from s to t.  Approximate: hubs = the n_hubs vertices of largest
+ * degree (ties to the smaller id); for each vertex s, d_s = distance to its
+ * nearest hub h(s) (ties to the lower hub rank) and r_s = radius_factor*d_s;
+ * D[s,t] = min(d_s + D(h(s),t), d_t + D(h(t),s), and the exact distance if
+ * it is <= r_s or <= r_t).  The approximate D is exactly symmetric. */
+int tmfg_apsp(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, int32_t dtype,
+              const int32_t *edges, const tmfg_apsp_params *params, float *D, int64_t ldd,
+              void *stream);
+
+/* Synchronise `stream`, then return the status word recorded by the
+ * context's kernels since the last call (TMFG_OK if none) and clear it. */
+int tmfg_sync_status(tmfg_ctx *ctx, void *stream);
+
+/* Counters of the last tmfg_build, valid after tmfg_sync_status:
+ * out[0] = face evaluations, out[1] = stale heap pops, out[2] = pointer
+ * scan chunks loaded, out[3] = insertion rounds, out[4] = loop time in ns
+ * (device clock).  `count` <= 8 entries are written. */
+int tmfg_last_stats(tmfg_ctx *ctx, int64_t *out, int count);
+
+/* Static description of a return code. */
+const char *tmfg_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TMFG_H */

@@ -64,6 +64,10 @@ def _load():
             lib.oracle_apsp_exact.restype = ci
             lib.oracle_sssp_rows.argtypes = [P, i64, i64, ci, P, i64, ci, P, i64, P]
             lib.oracle_sssp_rows.restype = ci
+            lib.oracle_sssp_bounded_rows.argtypes = [P, i64, i64, ci, P, i64, ci, P, P, i64, P]
+            lib.oracle_sssp_bounded_rows.restype = ci
+            lib.oracle_rowsort_rows.argtypes = [P, i64, i64, ci, P, i64, P]
+            lib.oracle_rowsort_rows.restype = ci
             lib.oracle_hubs.argtypes = [i64, P, i64, i64, P]
             lib.oracle_hubs.restype = ci
             lib.oracle_apsp_approx.argtypes = [P, i64, i64, ci, P, i64, i64, ctypes.c_double, ci,
@@ -171,6 +175,31 @@ def sssp_rows(S, edges, sources, prec: int = 64):
     _check(_load().oracle_sssp_rows(_ptr(S), n, S.shape[1], dt, _ptr(edges), edges.shape[0],
                                     prec, _ptr(src), src.shape[0], _ptr(D)), "sssp_rows")
     return D
+
+
+def sssp_bounded_rows(S, edges, sources, bounds, prec: int = 32):
+    """Radius-bounded searches from the given sources (Section 4.3)."""
+    S, dt = _mat(S)
+    n = S.shape[0]
+    edges = np.ascontiguousarray(edges, np.int32)
+    src = np.ascontiguousarray(sources, np.int32)
+    b = np.ascontiguousarray(bounds, np.float64)
+    D = np.empty((src.shape[0], n), np.float64)
+    _check(_load().oracle_sssp_bounded_rows(_ptr(S), n, S.shape[1], dt, _ptr(edges),
+                                            edges.shape[0], prec, _ptr(src), _ptr(b),
+                                            src.shape[0], _ptr(D)), "sssp_bounded_rows")
+    return D
+
+
+def rowsort_rows(S, rows):
+    """Sorted rows (R3) for the listed rows only: (len(rows), n-1) int32."""
+    S, dt = _mat(S)
+    n = S.shape[0]
+    r = np.ascontiguousarray(rows, np.int32)
+    out = np.empty((r.shape[0], n - 1), np.int32)
+    _check(_load().oracle_rowsort_rows(_ptr(S), n, S.shape[1], dt, _ptr(r), r.shape[0],
+                                       _ptr(out)), "rowsort_rows")
+    return out
 
 
 def hubs(n, edges, h):

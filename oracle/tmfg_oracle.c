@@ -753,6 +753,47 @@ int oracle_sssp_rows(const void *S, int64_t n, int64_t ld, int dtype, const int3
     return rc;
 }
 
+/* Bounded searches: for each listed source, Dijkstra that does not expand
+ * vertices farther than bound[i] (the radius search of Section 4.3).  Row i
+ * of D holds the distances found (exact for every vertex within the bound). */
+int oracle_sssp_bounded_rows(const void *S, int64_t n, int64_t ld, int dtype,
+                             const int32_t *edges, int64_t ne, int prec, const int32_t *src,
+                             const double *bound, int64_t nsrc, double *D)
+{
+    if (n < 1 || (prec != 32 && prec != 64)) return OR_EINVAL;
+    mat_t m = {S, n, ld, dtype};
+    graph_t g;
+    int rc = build_graph(&m, n, edges, ne, prec, &g);
+    if (rc) return rc;
+    uint8_t *done = (uint8_t *)malloc((size_t)n);
+    dent_t *heap = (dent_t *)malloc(sizeof(dent_t) * (size_t)(2 * ne + n + 1));
+    if (!done || !heap) rc = OR_ENOMEM;
+    for (int64_t i = 0; i < nsrc && !rc; ++i)
+        dijkstra(&g, src[i], prec, bound[i], D + i * n, done, heap);
+    free(done); free(heap);
+    graph_free(&g);
+    return rc;
+}
+
+/* Rows of the per-row sort for the listed rows only (same order as R3). */
+int oracle_rowsort_rows(const void *S, int64_t n, int64_t ld, int dtype, const int32_t *rows,
+                        int64_t nrows, int32_t *idx)
+{
+    if (n < 2) return OR_EINVAL;
+    mat_t m = {S, n, ld, dtype};
+    su_t *buf = (su_t *)malloc(sizeof(su_t) * (size_t)n);
+    if (!buf) return OR_ENOMEM;
+    for (int64_t i = 0; i < nrows; ++i) {
+        int64_t v = rows[i], k = 0;
+        for (int64_t u = 0; u < n; ++u)
+            if (u != v) { buf[k].s = sget(&m, v, u); buf[k].u = (int32_t)u; ++k; }
+        qsort(buf, (size_t)k, sizeof(su_t), cmp_su);
+        for (int64_t j = 0; j < k; ++j) idx[i * (n - 1) + j] = buf[j].u;
+    }
+    free(buf);
+    return OR_OK;
+}
+
 /* Hubs (R12): the h vertices of largest TMFG degree, ties to the smaller id,
  * listed in that rank order. */
 int oracle_hubs(int64_t n, const int32_t *edges, int64_t ne, int64_t h, int32_t *hubs)

@@ -1,1 +1,246 @@
-"""GB300-native TMFG construction and APSP over the TMFG (arXiv 2408.09399)."""
+"""GB300-native TMFG construction and APSP over the TMFG (arXiv 2408.09399).
+
+A thin ctypes binding over ``libtmfg.so`` (C ABI in ``include/tmfg.h``).
+Each function has the name of the C entry point it calls and only marshals
+arguments: torch CUDA tensors become device pointers, the current (or given)
+torch stream becomes the cudaStream_t.  Every step of the computation runs in
+the library's CUDA kernels; there is no CPU path.  Importing this package
+does not load the library; the first call does, and raises if it is missing
+or no CUDA device is present.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtmfg.so")
+
+TMFG_F32, TMFG_F64 = 0, 1
+TMFG_CORR, TMFG_HEAP = 0, 1
+TMFG_CHECK_SYMMETRY = 1
+ERRORS = {0: "TMFG_OK", 1: "TMFG_EINVAL", 2: "TMFG_ENOMEM", 3: "TMFG_ENONFINITE",
+          4: "TMFG_EASYMMETRIC", 5: "TMFG_ETIMEOUT", 6: "TMFG_ECUDA", 7: "TMFG_ERANGE",
+          8: "TMFG_ETOOBIG", 9: "TMFG_EINTERNAL"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class TmfgError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({_strerror(code)})")
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("prefix", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("flags", ctypes.c_uint32)]
+
+
+class _ApspParams(ctypes.Structure):
+    _fields_ = [("approx", ctypes.c_int32), ("n_hubs", ctypes.c_int32),
+                ("radius_factor", ctypes.c_float)]
+
+
+def load_library():
+    """Load libtmfg.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libtmfg.so not built ({LIB_PATH}); run "
+                               "paper_2408_09399_gb300.build.build() first")
+        lib = ctypes.CDLL(LIB_PATH)
+        P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        lib.tmfg_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.c_size_t]
+        lib.tmfg_create.restype = ctypes.c_int
+        lib.tmfg_destroy.argtypes = [P]
+        lib.tmfg_destroy.restype = None
+        lib.tmfg_max_n.argtypes = [ctypes.c_int]
+        lib.tmfg_max_n.restype = i64
+        lib.tmfg_workspace_bytes.argtypes = [i64, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        lib.tmfg_workspace_bytes.restype = ctypes.c_size_t
+        lib.tmfg_build.argtypes = [P, P, i64, i64, ctypes.POINTER(_Params), P, P, P, P, P]
+        lib.tmfg_build.restype = ctypes.c_int
+        lib.tmfg_row_sort.argtypes = [P, P, i64, i64, i32, P, i64, P, P]
+        lib.tmfg_row_sort.restype = ctypes.c_int
+        lib.tmfg_apsp.argtypes = [P, P, i64, i64, i32, P, ctypes.POINTER(_ApspParams), P, i64, P]
+        lib.tmfg_apsp.restype = ctypes.c_int
+        lib.tmfg_sync_status.argtypes = [P, P]
+        lib.tmfg_sync_status.restype = ctypes.c_int
+        lib.tmfg_last_stats.argtypes = [P, P, ctypes.c_int]
+        lib.tmfg_last_stats.restype = ctypes.c_int
+        lib.tmfg_strerror.argtypes = [ctypes.c_int]
+        lib.tmfg_strerror.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _strerror(code: int) -> str:
+    try:
+        return load_library().tmfg_strerror(int(code)).decode()
+    except Exception:  # library not loadable: keep the numeric code
+        return str(code)
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise TmfgError(code, where)
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libtmfg needs a CUDA device; none is available")
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t, dtype=None, what="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{what} must have dtype {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _mat_dtype(S):
+    torch = _torch()
+    if S.dim() != 2 or S.shape[0] != S.shape[1]:
+        raise ValueError("S must be a square matrix")
+    if S.stride(1) != 1:
+        raise ValueError("S must be row-major with unit column stride")
+    if S.dtype == torch.float32:
+        return TMFG_F32
+    if S.dtype == torch.float64:
+        return TMFG_F64
+    raise TypeError("S must be float32 or float64")
+
+
+class Context:
+    """Owns a tmfg_ctx (device status word + workspace)."""
+
+    def __init__(self, device: int = 0, workspace_budget_bytes: int = 0):
+        lib = load_library()
+        _torch()
+        h = ctypes.c_void_p()
+        _check(lib.tmfg_create(ctypes.byref(h), int(device), int(workspace_budget_bytes)),
+               "tmfg_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().tmfg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tmfg_create(device: int = 0, workspace_budget_bytes: int = 0) -> Context:
+    return Context(device, workspace_budget_bytes)
+
+
+def tmfg_destroy(ctx: Context):
+    ctx.close()
+
+
+def tmfg_max_n(dtype: int = TMFG_F32) -> int:
+    return int(load_library().tmfg_max_n(int(dtype)))
+
+
+def tmfg_workspace_bytes(n: int, dtype: int = TMFG_F32, what: int = 0, n_hubs: int = 0) -> int:
+    return int(load_library().tmfg_workspace_bytes(int(n), int(dtype), int(what), int(n_hubs)))
+
+
+def tmfg_build(ctx: Context, S, mode: str = "heap", prefix: int = 1, check_symmetry: bool = False,
+               out=None, stream=None):
+    """TMFG of S (a square CUDA tensor).  Returns dict of int32 CUDA tensors
+    order (n), edges (3n-6, 2), ins_face (n-4, 3), bubble_parent (n-3).
+    Asynchronous: call tmfg_sync_status to wait and read data errors."""
+    torch = _torch()
+    n = S.shape[0]
+    dt = _mat_dtype(S)
+    if out is None:
+        dev = S.device
+        out = {"order": torch.empty(n, dtype=torch.int32, device=dev),
+               "edges": torch.empty((max(3 * n - 6, 0), 2), dtype=torch.int32, device=dev),
+               "ins_face": torch.empty((max(n - 4, 0), 3), dtype=torch.int32, device=dev),
+               "bubble_parent": torch.empty(max(n - 3, 0), dtype=torch.int32, device=dev)}
+    p = _Params({"corr": TMFG_CORR, "heap": TMFG_HEAP}[mode], int(prefix), dt,
+                TMFG_CHECK_SYMMETRY if check_symmetry else 0)
+    i32 = torch.int32
+    rc = load_library().tmfg_build(ctx.handle, _dev_ptr(S), n, S.stride(0), ctypes.byref(p),
+                                   _dev_ptr(out["order"], i32), _dev_ptr(out["edges"], i32),
+                                   _dev_ptr(out["ins_face"], i32) if n > 4 else None,
+                                   _dev_ptr(out["bubble_parent"], i32), _stream_handle(stream))
+    _check(rc, "tmfg_build")
+    return out
+
+
+def tmfg_row_sort(ctx: Context, S, idx=None, rowsum=None, stream=None):
+    """Sorted index rows (uint16 stored in an int16 tensor, n x ldi) and int64
+    row sums of S.  Returns (idx, rowsum)."""
+    torch = _torch()
+    n = S.shape[0]
+    dt = _mat_dtype(S)
+    if idx is None:
+        ldi = ((n - 1) + 7) // 8 * 8
+        idx = torch.empty((n, ldi), dtype=torch.int16, device=S.device)
+    if rowsum is None:
+        rowsum = torch.empty(n, dtype=torch.int64, device=S.device)
+    rc = load_library().tmfg_row_sort(ctx.handle, _dev_ptr(S), n, S.stride(0), dt,
+                                      _dev_ptr(idx, torch.int16), idx.stride(0),
+                                      _dev_ptr(rowsum, torch.int64), _stream_handle(stream))
+    _check(rc, "tmfg_row_sort")
+    return idx, rowsum
+
+
+def tmfg_apsp(ctx: Context, S, edges, approx: bool = False, n_hubs: int = 0,
+              radius_factor: float = 0.0, D=None, stream=None):
+    """Shortest-path distances over the TMFG given by ``edges`` (int32 CUDA
+    tensor, 3n-6 x 2).  Returns D (float32 CUDA tensor, n x n)."""
+    torch = _torch()
+    n = S.shape[0]
+    dt = _mat_dtype(S)
+    if D is None:
+        D = torch.empty((n, n), dtype=torch.float32, device=S.device)
+    p = _ApspParams(1 if approx else 0, int(n_hubs), float(radius_factor))
+    rc = load_library().tmfg_apsp(ctx.handle, _dev_ptr(S), n, S.stride(0), dt,
+                                  _dev_ptr(edges.contiguous(), torch.int32), ctypes.byref(p),
+                                  _dev_ptr(D, torch.float32), D.stride(0), _stream_handle(stream))
+    _check(rc, "tmfg_apsp")
+    return D
+
+
+def tmfg_sync_status(ctx: Context, stream=None, raise_on_error: bool = True) -> int:
+    """Wait for the stream, then return (or raise) the recorded status."""
+    code = load_library().tmfg_sync_status(ctx.handle, _stream_handle(stream))
+    if raise_on_error:
+        _check(code, "device status")
+    return int(code)
+
+
+def tmfg_last_stats(ctx: Context) -> dict:
+    arr = (ctypes.c_int64 * 8)()
+    _check(load_library().tmfg_last_stats(ctx.handle, arr, 8), "tmfg_last_stats")
+    keys = ["face_evals", "stale_pops", "scan_chunks", "rounds", "loop_ns"]
+    return {k: int(arr[i]) for i, k in enumerate(keys)}
+
+
+def tmfg_strerror(code: int) -> str:
+    return _strerror(code)

@@ -1,0 +1,380 @@
+// rowsort.cu -- per-row key/index sort of S and exact row sums
+// (Algorithm 1, sort loop and initial 4-clique row sums).
+//
+// One CTA sorts one row at a time (persistent grid, one CTA per SM):
+//   * the row is read once from HBM with 16-byte loads, each entry mapped
+//     to a 32-bit (float) or 64-bit (double) unsigned key whose ascending
+//     order is descending similarity (-0.0 folded into +0.0);
+//   * the same pass accumulates the exact row sum sum_u q(S[v,u]) in int64
+//     (q = x*2^40 rounded to nearest-even, order independent) and checks that
+//     every off-diagonal entry is finite with |x| <= 64;
+//   * a stable LSD radix sort on 8-bit digits runs in shared memory; ranks
+//     inside a warp come from __match_any_sync, ranks across warps from a
+//     block-wide scan of per-warp digit counts (digit-major), which keeps
+//     equal keys in ascending column order: (S desc, u asc);
+//   * for float rows the key shrinks by 8 bits per pass (32 -> 24 -> 16 -> 8
+//     -> 0) and is packed with the 16-bit position, so the whole row needs
+//     10 bytes of shared memory per entry (n up to 21581);
+//   * the sorted positions are converted to vertex ids (skipping the
+//     diagonal) and written with 16-byte stores, rows padded to ldi with
+//     0xFFFF.
+#include "internal.cuh"
+
+namespace tmfg {
+
+constexpr int kSortThreads = 512;
+constexpr int kSortWarps = kSortThreads / kWarp;
+constexpr int kHistBytes = kSortWarps * 256 * 4;
+constexpr int kSortSmemMax = 232448;  // 227 KB opt-in shared memory per CTA
+
+__host__ __device__ constexpr int sort_smem_f32(int m) { return kHistBytes + 256 + 10 * m + 64; }
+__host__ __device__ constexpr int sort_smem_f64(int m) { return kHistBytes + 256 + 20 * m + 64; }
+
+// Block-wide exclusive scan of the per-warp digit counts, digit-major
+// (digit d of warp w gets sum of all counts with smaller digit, plus the
+// counts of digit d in warps before w).  hist[w*256 + d] is replaced by
+// that offset.
+__device__ __forceinline__ void scan_hist(uint32_t *hist, uint32_t *wsum)
+{
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // thread t owns digit d = t>>1 and warps [8*(t&1), 8*(t&1)+8)
+    const int d = t >> 1, w0 = (t & 1) * (kSortWarps / 2);
+    uint32_t v[kSortWarps / 2];
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kSortWarps / 2; ++i) {
+        v[i] = hist[(w0 + i) * 256 + d];
+        s += v[i];
+    }
+    // inclusive warp scan of s
+    uint32_t x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t ws = lane < kSortWarps ? wsum[lane] : 0;
+        uint32_t z = ws;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
+        }
+        if (lane < kSortWarps) wsum[lane] = z - ws;  // exclusive
+    }
+    __syncthreads();
+    uint32_t run = wsum[warp] + x - s;
+#pragma unroll
+    for (int i = 0; i < kSortWarps / 2; ++i) {
+        hist[(w0 + i) * 256 + d] = run;
+        run += v[i];
+    }
+    __syncthreads();
+}
+
+// One stable counting pass over m entries held warp-striped: warp w owns
+// positions [w*32*I, (w+1)*32*I), lane l position base + j*32 + l.
+// digit_of(p) gives the 8-bit digit of the entry at position p; emit(p, q)
+// moves it to position q of the destination buffer.
+template <int I, class DigitOf, class Emit>
+__device__ __forceinline__ void radix_pass(int m, uint32_t *hist, uint32_t *wsum,
+                                           DigitOf digit_of, Emit emit)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *h = hist + warp * 256;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) h[lane + 32 * i] = 0;
+    __syncwarp();
+    const int base = warp * 32 * I;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t rank[I];
+#pragma unroll
+    for (int j = 0; j < I; ++j) {
+        const int p = base + j * 32 + lane;
+        const bool valid = p < m;
+        const uint32_t d = valid ? digit_of(p) : 0x100u + lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        uint32_t before = valid ? h[d] : 0u;
+        rank[j] = before + __popc(peers & lt);
+        __syncwarp();
+        if (valid && (peers & lt) == 0) h[d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    scan_hist(hist, wsum);
+#pragma unroll
+    for (int j = 0; j < I; ++j) {
+        const int p = base + j * 32 + lane;
+        if (p < m) emit(p, h[digit_of(p)] + rank[j]);
+    }
+    __syncthreads();
+}
+
+// Sum an int64 over the block; result valid in thread 0.
+__device__ __forceinline__ long long block_sum_ll(long long x, long long *red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) red[warp] = x;
+    __syncthreads();
+    long long s = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kSortWarps; ++w) s += red[w];
+    __syncthreads();
+    return s;
+}
+
+// Write the sorted row: positions -> vertex ids (skip the diagonal), pad
+// to ldi with 0xFFFF.
+__device__ __forceinline__ void store_row(const uint16_t *pos, int m, int v, uint16_t *out,
+                                          long long ldi, bool vec)
+{
+    if (vec) {
+        const int chunks = (int)(ldi / 8);
+        for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+            uint16_t e[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int j = c * 8 + k;
+                if (j < m) {
+                    const int p = pos[j];
+                    e[k] = (uint16_t)(p + (p >= v));
+                } else {
+                    e[k] = kNone16;
+                }
+            }
+            uint4 q;
+            q.x = e[0] | ((uint32_t)e[1] << 16);
+            q.y = e[2] | ((uint32_t)e[3] << 16);
+            q.z = e[4] | ((uint32_t)e[5] << 16);
+            q.w = e[6] | ((uint32_t)e[7] << 16);
+            reinterpret_cast<uint4 *>(out)[c] = q;
+        }
+    } else {
+        for (int j = threadIdx.x; j < m; j += blockDim.x) {
+            const int p = pos[j];
+            out[j] = (uint16_t)(p + (p >= v));
+        }
+    }
+}
+
+// ---------------------------------------------------------------- float rows
+template <int I>
+__global__ void __launch_bounds__(kSortThreads, 1)
+rowsort_f32_kernel(const float *__restrict__ S, int n, long long ld, bool vec_in,
+                   uint16_t *__restrict__ idx, long long ldi, bool vec_out,
+                   long long *__restrict__ rowsum, int *status)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int m = n - 1;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *wsum = reinterpret_cast<uint32_t *>(smem + kHistBytes);
+    long long *red = reinterpret_cast<long long *>(smem + kHistBytes + 64);
+    unsigned char *r1 = smem + kHistBytes + 256;  // 4m bytes: KEY0, then P2, then OUT16
+    const int r1_bytes = ((4 * m + 15) / 16) * 16;
+    unsigned char *r2 = r1 + r1_bytes;            // 6m bytes: P1 (key24 + pos), then P3
+    uint32_t *key0 = reinterpret_cast<uint32_t *>(r1);
+    uint32_t *p2 = reinterpret_cast<uint32_t *>(r1);
+    uint16_t *out16 = reinterpret_cast<uint16_t *>(r1);
+    uint32_t *p1k = reinterpret_cast<uint32_t *>(r2);
+    uint16_t *p1v = reinterpret_cast<uint16_t *>(r2 + 4 * (size_t)m);
+    uint32_t *p3 = reinterpret_cast<uint32_t *>(r2);
+
+    for (int v = blockIdx.x; v < n; v += gridDim.x) {
+        const float *row = S + (long long)v * ld;
+        long long acc = 0;
+        int bad = 0;
+        auto take = [&](int u, float x) {
+            if (u == v) return;
+            x = canon(x);
+            int c = check_entry(x);
+            if (c) bad = c;
+            acc += quantize40(x);
+            key0[u - (u > v)] = ~ord_key(x);  // ascending key = descending S
+        };
+        if (vec_in) {
+            const int n4 = n >> 2;
+            const float4 *row4 = reinterpret_cast<const float4 *>(row);
+            for (int q = threadIdx.x; q < n4; q += blockDim.x) {
+                float4 x = __ldcs(row4 + q);
+                take(4 * q, x.x);
+                take(4 * q + 1, x.y);
+                take(4 * q + 2, x.z);
+                take(4 * q + 3, x.w);
+            }
+            for (int u = 4 * n4 + threadIdx.x; u < n; u += blockDim.x) take(u, row[u]);
+        } else {
+            for (int u = threadIdx.x; u < n; u += blockDim.x) take(u, row[u]);
+        }
+        if (bad) set_status(status, bad);
+        __syncthreads();
+        const long long rs = block_sum_ll(acc, red);
+        if (threadIdx.x == 0 && rowsum) rowsum[v] = rs;
+
+        radix_pass<I>(m, hist, wsum,
+            [&](int p) { return key0[p] & 0xFFu; },
+            [&](int p, uint32_t q) { p1k[q] = key0[p] >> 8; p1v[q] = (uint16_t)p; });
+        radix_pass<I>(m, hist, wsum,
+            [&](int p) { return p1k[p] & 0xFFu; },
+            [&](int p, uint32_t q) { p2[q] = ((p1k[p] >> 8) << 16) | p1v[p]; });
+        radix_pass<I>(m, hist, wsum,
+            [&](int p) { return (p2[p] >> 16) & 0xFFu; },
+            [&](int p, uint32_t q) { p3[q] = ((p2[p] >> 24) << 16) | (p2[p] & 0xFFFFu); });
+        radix_pass<I>(m, hist, wsum,
+            [&](int p) { return p3[p] >> 16; },
+            [&](int p, uint32_t q) { out16[q] = (uint16_t)(p3[p] & 0xFFFFu); });
+
+        store_row(out16, m, v, idx + (long long)v * ldi, ldi, vec_out);
+        __syncthreads();
+    }
+}
+
+// --------------------------------------------------------------- double rows
+template <int I>
+__global__ void __launch_bounds__(kSortThreads, 1)
+rowsort_f64_kernel(const double *__restrict__ S, int n, long long ld, bool vec_in,
+                   uint16_t *__restrict__ idx, long long ldi, bool vec_out,
+                   long long *__restrict__ rowsum, int *status)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int m = n - 1;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *wsum = reinterpret_cast<uint32_t *>(smem + kHistBytes);
+    long long *red = reinterpret_cast<long long *>(smem + kHistBytes + 64);
+    unsigned char *base = smem + kHistBytes + 256;
+    uint64_t *k0 = reinterpret_cast<uint64_t *>(base);
+    uint64_t *k1 = k0 + m;
+    uint16_t *v0 = reinterpret_cast<uint16_t *>(k1 + m);
+    uint16_t *v1 = v0 + m;
+
+    for (int v = blockIdx.x; v < n; v += gridDim.x) {
+        const double *row = S + (long long)v * ld;
+        long long acc = 0;
+        int bad = 0;
+        auto take = [&](int u, double x) {
+            if (u == v) return;
+            x = canon(x);
+            int c = check_entry(x);
+            if (c) bad = c;
+            acc += quantize40(x);
+            k0[u - (u > v)] = ~ord_key(x);
+        };
+        if (vec_in) {
+            const int n2 = n >> 1;
+            const double2 *row2 = reinterpret_cast<const double2 *>(row);
+            for (int q = threadIdx.x; q < n2; q += blockDim.x) {
+                double2 x = __ldcs(row2 + q);
+                take(2 * q, x.x);
+                take(2 * q + 1, x.y);
+            }
+            for (int u = 2 * n2 + threadIdx.x; u < n; u += blockDim.x) take(u, row[u]);
+        } else {
+            for (int u = threadIdx.x; u < n; u += blockDim.x) take(u, row[u]);
+        }
+        if (bad) set_status(status, bad);
+        __syncthreads();
+        const long long rs = block_sum_ll(acc, red);
+        if (threadIdx.x == 0 && rowsum) rowsum[v] = rs;
+
+        // pass 0: positions are implicit
+        radix_pass<I>(m, hist, wsum,
+            [&](int p) { return (uint32_t)(k0[p] & 0xFFu); },
+            [&](int p, uint32_t q) { k1[q] = k0[p]; v1[q] = (uint16_t)p; });
+#pragma unroll 1
+        for (int pass = 1; pass < 8; ++pass) {
+            const int sh = 8 * pass;
+            uint64_t *ks = (pass & 1) ? k1 : k0;
+            uint64_t *kd = (pass & 1) ? k0 : k1;
+            uint16_t *vs = (pass & 1) ? v1 : v0;
+            uint16_t *vd = (pass & 1) ? v0 : v1;
+            radix_pass<I>(m, hist, wsum,
+                [&](int p) { return (uint32_t)((ks[p] >> sh) & 0xFFu); },
+                [&](int p, uint32_t q) { kd[q] = ks[p]; vd[q] = vs[p]; });
+        }
+        // after 8 passes the result is in (k0, v0)
+        store_row(v0, m, v, idx + (long long)v * ldi, ldi, vec_out && ((uintptr_t)v0 % 16 == 0));
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------- launch
+static int pick_items(int m, const int *choices, int nc)
+{
+    for (int i = 0; i < nc; ++i)
+        if ((long long)choices[i] * kSortThreads >= m) return choices[i];
+    return -1;
+}
+
+int64_t rowsort_max_n(int dtype)
+{
+    // largest n whose row fits in shared memory and in the largest I
+    if (dtype == TMFG_F32) {
+        int m = (kSortSmemMax - kHistBytes - 256 - 64) / 10;
+        m = m < 43 * kSortThreads ? m : 43 * kSortThreads;
+        return m + 1;
+    }
+    int m = (kSortSmemMax - kHistBytes - 256 - 64) / 20;
+    m = m < 22 * kSortThreads ? m : 22 * kSortThreads;
+    return m + 1;
+}
+
+#define TMFG_LAUNCH_SORT(KER, II)                                                              \
+    case II: {                                                                                 \
+        auto k = KER<II>;                                                                      \
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=      \
+            cudaSuccess)                                                                       \
+            return TMFG_ECUDA;                                                                 \
+        k<<<grid, kSortThreads, smem, stream>>>(reinterpret_cast<const ET *>(S), n, ld,        \
+                                                vec_in, idx, ldi, vec_out, rowsum, status);    \
+        break;                                                                                 \
+    }
+
+int launch_rowsort(const void *S, int n, long long ld, int dtype, uint16_t *idx, long long ldi,
+                   long long *rowsum, int *status, int num_sms, cudaStream_t stream)
+{
+    const int m = n - 1;
+    const bool vec_out = (ldi % 8 == 0) && ((uintptr_t)idx % 16 == 0);
+    const int grid = n < num_sms ? n : num_sms;
+    if (dtype == TMFG_F32) {
+        using ET = float;
+        static const int choices[] = {1, 2, 4, 8, 16, 24, 32, 43};
+        const int I = pick_items(m, choices, 8);
+        const int smem = sort_smem_f32(m);
+        if (I < 0 || smem > kSortSmemMax) return TMFG_ETOOBIG;
+        const bool vec_in = (ld % 4 == 0) && ((uintptr_t)S % 16 == 0);
+        switch (I) {
+            TMFG_LAUNCH_SORT(rowsort_f32_kernel, 1)
+            TMFG_LAUNCH_SORT(rowsort_f32_kernel, 2)
+            TMFG_LAUNCH_SORT(rowsort_f32_kernel, 4)
+            TMFG_LAUNCH_SORT(rowsort_f32_kernel, 8)
+            TMFG_LAUNCH_SORT(rowsort_f32_kernel, 16)
+            TMFG_LAUNCH_SORT(rowsort_f32_kernel, 24)
+            TMFG_LAUNCH_SORT(rowsort_f32_kernel, 32)
+            TMFG_LAUNCH_SORT(rowsort_f32_kernel, 43)
+            default: return TMFG_EINTERNAL;
+        }
+    } else {
+        using ET = double;
+        static const int choices[] = {1, 2, 4, 8, 16, 22};
+        const int I = pick_items(m, choices, 6);
+        const int smem = sort_smem_f64(m);
+        if (I < 0 || smem > kSortSmemMax) return TMFG_ETOOBIG;
+        const bool vec_in = (ld % 2 == 0) && ((uintptr_t)S % 16 == 0);
+        switch (I) {
+            TMFG_LAUNCH_SORT(rowsort_f64_kernel, 1)
+            TMFG_LAUNCH_SORT(rowsort_f64_kernel, 2)
+            TMFG_LAUNCH_SORT(rowsort_f64_kernel, 4)
+            TMFG_LAUNCH_SORT(rowsort_f64_kernel, 8)
+            TMFG_LAUNCH_SORT(rowsort_f64_kernel, 16)
+            TMFG_LAUNCH_SORT(rowsort_f64_kernel, 22)
+            default: return TMFG_EINTERNAL;
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? TMFG_OK : TMFG_ECUDA;
+}
+
+}  // namespace tmfg

@@ -1,0 +1,264 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+TMFG outputs (order, edges, faces used, bubble parents) and the sorted rows
+must match bit for bit; APSP must match the oracle's float path-sum
+arithmetic bit for bit and the double-precision oracle within 1e-5 relative
+(the tolerance stated for the APSP in FP32).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_09399_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_traced_tmfg.json")
+MODES = [("corr", 1), ("corr", 2), ("corr", 10), ("heap", 1)]
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_09399_gb300 import build
+    build.build()
+    import paper_2408_09399_gb300 as T
+    return T
+
+
+@pytest.fixture(scope="module")
+def ctx(T):
+    c = T.tmfg_create(0)
+    yield c
+    c.close()
+
+
+def dev(S):
+    return torch.as_tensor(np.ascontiguousarray(S), device="cuda:0")
+
+
+def run_tmfg(T, ctx, S, mode, P):
+    out = T.tmfg_build(ctx, dev(S), mode, P)
+    T.tmfg_sync_status(ctx)
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def assert_tmfg_equal(got, ref, tag=""):
+    assert np.array_equal(got["order"], ref["order"]), f"order {tag}"
+    assert np.array_equal(got["edges"], ref["edges"]), f"edges {tag}"
+    assert np.array_equal(got["ins_face"], ref["ins_face"]), f"ins_face {tag}"
+    assert np.array_equal(got["bubble_parent"], ref["parent"]), f"parent {tag}"
+
+
+# ------------------------------------------------------------------ row sort
+
+@pytest.mark.parametrize("n", [5, 6, 37, 200, 513, 1031, 2050])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("kind", ["uniform", "quantized", "constant"])
+def test_row_sort_bit_exact(T, ctx, n, dtype, kind):
+    S = W.random_similarity(1000 + n, n, dtype, kind)
+    idx, rs = T.tmfg_row_sort(ctx, dev(S))
+    T.tmfg_sync_status(ctx)
+    got = idx.cpu().numpy().view(np.uint16)[:, : n - 1].astype(np.int32)
+    assert np.array_equal(got, oracle.rowsort(S))
+    assert np.array_equal(rs.cpu().numpy(), oracle.rowsums(S))
+    assert np.all(idx.cpu().numpy().view(np.uint16)[:, n - 1:] == 0xFFFF)
+
+
+def test_row_sort_strided_input(T, ctx):
+    n = 301
+    S = W.random_similarity(7, n, np.float32)
+    big = np.zeros((n, n + 3), np.float32)
+    big[:, :n] = S
+    dS = torch.as_tensor(big, device="cuda:0")[:, :n]
+    idx, rs = T.tmfg_row_sort(ctx, dS)
+    T.tmfg_sync_status(ctx)
+    assert np.array_equal(idx.cpu().numpy().view(np.uint16)[:, : n - 1].astype(np.int32),
+                          oracle.rowsort(S))
+
+
+# ------------------------------------------------------------------ TMFG
+
+def test_hand_traced_cases(T, ctx):
+    for case in json.load(open(GOLDEN))["cases"]:
+        n = case["n"]
+        S = np.eye(n)
+        if "constant_64ths" in case:
+            S[:] = case["constant_64ths"] / 64.0
+            np.fill_diagonal(S, 1.0)
+        else:
+            for key, val in case["upper_64ths"].items():
+                i, j = map(int, key.split(","))
+                S[i, j] = S[j, i] = val / 64.0
+        for dtype in (np.float32, np.float64):
+            for key, exp in case["expect"].items():
+                if key == "exact":
+                    continue
+                mode, P = {"corr1": ("corr", 1), "corr2": ("corr", 2), "heap": ("heap", 1)}[key]
+                got = run_tmfg(T, ctx, S.astype(dtype), mode, P)
+                assert got["order"].tolist() == exp["order"], (case["name"], key)
+                assert got["ins_face"].tolist() == exp["ins_face"], (case["name"], key)
+                assert got["bubble_parent"].tolist() == exp["parent"], (case["name"], key)
+                if key == "heap":
+                    assert T.tmfg_last_stats(ctx)["stale_pops"] == exp["stale_pops"]
+
+
+@pytest.mark.parametrize("n", [4, 5, 6, 7, 33, 100, 257, 600])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_tmfg_small_random(T, ctx, n, dtype):
+    for kind in ("uniform", "quantized"):
+        S = W.random_similarity(2000 + n, n, dtype, kind)
+        for mode, P in MODES:
+            ref = oracle.tmfg(S, mode, P)
+            assert_tmfg_equal(run_tmfg(T, ctx, S, mode, P), ref, f"{kind} {mode} {P}")
+
+
+def test_tmfg_constant_matrix_ties(T, ctx):
+    S = W.random_similarity(5, 60, np.float32, "constant")
+    for mode, P in MODES:
+        assert_tmfg_equal(run_tmfg(T, ctx, S, mode, P), oracle.tmfg(S, mode, P), f"{mode} {P}")
+
+
+def test_tmfg_config1_planted(T, ctx):
+    S, _ = W.config_similarity(1)
+    for mode, P in MODES:
+        assert_tmfg_equal(run_tmfg(T, ctx, S, mode, P), oracle.tmfg(S, mode, P), f"{mode} {P}")
+
+
+def test_tmfg_prefix_large(T, ctx):
+    S = W.random_similarity(9, 300, np.float32)
+    for P in (50, 200, 256):
+        assert_tmfg_equal(run_tmfg(T, ctx, S, "corr", P), oracle.tmfg(S, "corr", P), f"P={P}")
+
+
+def test_tmfg_deterministic(T, ctx):
+    S = W.random_similarity(11, 1500, np.float32)
+    a = run_tmfg(T, ctx, S, "heap", 1)
+    b = run_tmfg(T, ctx, S, "heap", 1)
+    for k in a:
+        assert np.array_equal(a[k], b[k])
+
+
+@pytest.mark.slow
+def test_tmfg_config2_all_modes(T, ctx):
+    S, _ = W.config_similarity(2)
+    for mode, P in [("corr", 1), ("corr", 10), ("heap", 1)]:
+        assert_tmfg_equal(run_tmfg(T, ctx, S, mode, P), oracle.tmfg(S, mode, P), f"{mode} {P}")
+
+
+# ------------------------------------------------------------------ APSP
+
+def run_apsp(T, ctx, S, edges, **kw):
+    D = T.tmfg_apsp(ctx, dev(S), torch.as_tensor(edges, device="cuda:0"), **kw)
+    T.tmfg_sync_status(ctx)
+    return D.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("n,dtype", [(5, np.float32), (40, np.float64), (257, np.float32),
+                                     (1000, np.float32), (1500, np.float64)])
+def test_apsp_exact_bit_exact(T, ctx, n, dtype):
+    S = W.random_similarity(3000 + n, n, dtype)
+    edges = oracle.tmfg(S, "heap")["edges"]
+    D = run_apsp(T, ctx, S, edges)
+    assert np.array_equal(D, oracle.apsp_exact(S, edges, prec=32))
+    np.testing.assert_allclose(D, oracle.apsp_exact(S, edges, prec=64), rtol=1e-5, atol=1e-7)
+
+
+@pytest.mark.parametrize("n", [40, 300, 1200])
+def test_apsp_approx_bit_exact(T, ctx, n):
+    S = W.random_similarity(4000 + n, n, np.float32)
+    edges = oracle.tmfg(S, "heap")["edges"]
+    for h, rf in [(0, 2.0), (5, 1.0), (n, 2.0), (1, 3.0)]:
+        D = run_apsp(T, ctx, S, edges, approx=True, n_hubs=h, radius_factor=rf)
+        ref, _ = oracle.apsp_approx(S, edges, h, rf, prec=32)
+        assert np.array_equal(D, ref), (h, rf)
+        assert np.array_equal(D, D.T)
+
+
+def test_apsp_config1(T, ctx):
+    S, _ = W.config_similarity(1)
+    edges = oracle.tmfg(S, "heap")["edges"]
+    D = run_apsp(T, ctx, S, edges)
+    np.testing.assert_allclose(D, oracle.apsp_exact(S, edges, prec=64), rtol=1e-5, atol=1e-7)
+    Da = run_apsp(T, ctx, S, edges, approx=True)
+    assert np.array_equal(Da, oracle.apsp_approx(S, edges, 0, 2.0, prec=32)[0])
+
+
+@pytest.mark.slow
+def test_apsp_config2(T, ctx):
+    S, _ = W.config_similarity(2)
+    edges = oracle.tmfg(S, "heap")["edges"]
+    D = run_apsp(T, ctx, S, edges)
+    assert np.array_equal(D, oracle.apsp_exact(S, edges, prec=32))
+    Da = run_apsp(T, ctx, S, edges, approx=True)
+    assert np.array_equal(Da, oracle.apsp_approx(S, edges, 0, 2.0, prec=32)[0])
+
+
+# ------------------------------------------------------------------ errors
+
+def test_data_errors_are_reported(T, ctx):
+    n = 50
+    S = W.random_similarity(21, n, np.float32)
+    bad = S.copy()
+    bad[3, 7] = np.nan
+    T.tmfg_build(ctx, dev(bad), "heap")
+    assert T.tmfg_sync_status(ctx, raise_on_error=False) == 3       # ENONFINITE
+    bad = S.copy()
+    bad[3, 7] = bad[7, 3] = 65.0
+    T.tmfg_build(ctx, dev(bad), "heap")
+    assert T.tmfg_sync_status(ctx, raise_on_error=False) == 7       # ERANGE
+    bad = S.copy()
+    bad[3, 7] += 0.25
+    T.tmfg_build(ctx, dev(bad), "heap", check_symmetry=True)
+    assert T.tmfg_sync_status(ctx, raise_on_error=False) == 4       # EASYMMETRIC
+    # the status was cleared: a good call works again
+    assert_tmfg_equal(run_tmfg(T, ctx, S, "heap", 1), oracle.tmfg(S, "heap"))
+
+
+def test_argument_errors(T, ctx):
+    S = dev(W.random_similarity(22, 20, np.float32))
+    with pytest.raises(T.TmfgError) as e:
+        T.tmfg_build(ctx, S, "heap", 2)
+    assert e.value.code == 1
+    with pytest.raises(T.TmfgError) as e:
+        T.tmfg_build(ctx, S, "corr", 0)
+    assert e.value.code == 1
+    big = T.tmfg_max_n(0) + 1
+    with pytest.raises(T.TmfgError) as e:
+        T.tmfg_build(ctx, torch.zeros((big, big), device="cuda:0"), "heap")
+    assert e.value.code == 8
+
+
+# ------------------------------------------------------------------ full size
+
+@pytest.mark.slow
+def test_full_size_n20000(T, ctx):
+    """The n=20000 workload in the benchmark's launch configuration: the
+    whole heap TMFG is compared with the oracle; APSP rows of 48 sampled
+    sources are compared bit for bit; the approximate matrix is checked for
+    its defining properties on sampled rows."""
+    S, _ = W.config_similarity(3, device="cuda")
+    Sn = S.cpu().numpy()
+    out = T.tmfg_build(ctx, S, "heap")
+    D = T.tmfg_apsp(ctx, S, out["edges"])
+    T.tmfg_sync_status(ctx)
+    ref = oracle.tmfg(Sn, "heap")
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    assert_tmfg_equal(got, ref, "n=20000 heap")
+    rng = np.random.default_rng(0)
+    src = np.unique(np.concatenate([[0, 19999], rng.integers(0, 20000, 46)]))
+    Dr = oracle.sssp_rows(Sn, ref["edges"], src, prec=32)
+    assert np.array_equal(D[torch.as_tensor(src, device="cuda:0")].cpu().numpy().astype(np.float64), Dr)
+    Da = T.tmfg_apsp(ctx, S, out["edges"], approx=True)
+    T.tmfg_sync_status(ctx)
+    Das = Da[torch.as_tensor(src, device="cuda:0")].cpu().numpy().astype(np.float64)
+    assert np.array_equal(Das, Da[:, torch.as_tensor(src, device="cuda:0")].T.cpu().numpy())
+    # min over estimates that include the search from t, whose float fold can
+    # end one rounding below the fold from s: compare within float rounding
+    assert np.all(Das >= Dr * (1 - 1e-6))
+    assert np.all(Das[Das < Dr] >= Dr[Das < Dr] * (1 - 1e-6))

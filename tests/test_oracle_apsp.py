@@ -153,3 +153,16 @@ def test_approx_ties_constant_lengths():
         assert np.any((HD == HD.min(axis=0)).sum(axis=0) > 1)
         assert np.all(info["nearest"] == np.argmin(HD, axis=0))
         assert np.all(Da >= Dx - 1e-6)
+
+
+def test_sampled_oracle_rows_match_full():
+    S, edges = tmfg_case(12, 70)
+    D = oracle.apsp_exact(S, edges, prec=32)
+    src = [3, 0, 69]
+    b = oracle.sssp_bounded_rows(S, edges, src, [np.inf, np.inf, np.inf])
+    assert np.array_equal(b, D[src])
+    b = oracle.sssp_bounded_rows(S, edges, src, [0.5, 1.0, 2.0])
+    for i, s in enumerate(src):
+        within = D[s] <= [0.5, 1.0, 2.0][i]
+        assert np.array_equal(b[i][within], D[s][within])
+    assert np.array_equal(oracle.rowsort_rows(S, [5, 0, 69]), oracle.rowsort(S)[[5, 0, 69]])

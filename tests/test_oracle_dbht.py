@@ -9,7 +9,6 @@ import numpy as np
 import pytest
 from scipy.cluster.hierarchy import fcluster, linkage
 from scipy.spatial.distance import squareform
-from sklearn.metrics import adjusted_rand_score
 
 import oracle
 from paper_2408_09399_gb300 import workloads as W
@@ -31,6 +30,7 @@ def partitions_of(Z, n):
 
 @pytest.mark.parametrize("seed,n", [(1, 10), (2, 40), (3, 90)])
 def test_complete_linkage_matches_scipy(seed, n):
+    adjusted_rand_score = pytest.importorskip("sklearn.metrics").adjusted_rand_score
     X = W.normal(seed, "pts", n * 3).reshape(n, 3)
     D = np.sqrt(((X[:, None, :] - X[None, :, :]) ** 2).sum(-1))
     Z = oracle.complete_linkage(D)
@@ -45,6 +45,7 @@ def test_complete_linkage_matches_scipy(seed, n):
 
 
 def test_ari_matches_sklearn():
+    adjusted_rand_score = pytest.importorskip("sklearn.metrics").adjusted_rand_score
     for seed in range(5):
         a = (W.u64(seed, "a", 300) % np.uint64(7)).astype(np.int32)
         b = (W.u64(seed, "b", 300) % np.uint64(5)).astype(np.int32)

@@ -131,6 +131,33 @@ int tmfg_apsp(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, int32_t dtype
               const int32_t *edges, const tmfg_apsp_params *params, float *D, int64_t ldd,
               void *stream);
 
+/* Largest n accepted by tmfg_apsp_exact_noalloc. */
+#define TMFG_NOALLOC_MAX_N 21581
+
+/* Exact APSP (same result, bit for bit, as tmfg_apsp with approx = 0) that
+ * allocates no device memory and needs no tmfg_ctx.  The paper has no
+ * counterpart: it is for callers that cannot call cudaMalloc -- a process
+ * whose device memory is all owned by its own pool or caching allocator,
+ * or a code path that must not take an allocator's locks and device
+ * synchronisation.  Its scratch (about 1.3 MB: the TMFG's adjacency in CSR
+ * form) is one static device array inside libtmfg.so, which every GPU that
+ * loads the library holds until the process exits.
+ *   S, n, ld, dtype, edges, D, ldd: as for tmfg_apsp.
+ *   status: caller-owned device int32; the call sets it to 0 and the
+ *           kernels record the first data error in it (read it after the
+ *           stream reaches this call).
+ * Runs on the current CUDA device.  The first call on a device looks up the
+ * scratch array's device address; make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's
+ * contents (the call clears what must start at zero): calls whose kernels
+ * overlap on the GPU, on different streams or threads, race and corrupt
+ * each other's results -- order them on one stream.
+ * Returns TMFG_ETOOBIG for n > TMFG_NOALLOC_MAX_N, TMFG_EINVAL for bad
+ * arguments, TMFG_ECUDA if the set-up or a launch fails. */
+int tmfg_apsp_exact_noalloc(const void *S, int64_t n, int64_t ld, int32_t dtype,
+                            const int32_t *edges, float *D, int64_t ldd, int32_t *status,
+                            void *stream);
+
 /* Synchronise `stream`, then return the status word recorded by the
  * context's kernels since the last call (TMFG_OK if none) and clear it. */
 int tmfg_sync_status(tmfg_ctx *ctx, void *stream);

@@ -22,6 +22,7 @@
 //   nearest_hub     per vertex, the closest hub (ties to the lower rank);
 //   sym_min         D = min(R, R^T) tile by tile (32x32), in place.
 #include <cfloat>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -471,3 +472,74 @@ int launch_apsp(const void *S, int n, long long ld, int dtype, const int *edges,
 }
 
 }  // namespace tmfg
+
+// ------------------------------------------------- allocation-free variant
+// Exact APSP whose scratch (the CSR: degrees, row pointers, cursors, arcs)
+// lives in one file-scope device array instead of a context workspace, for
+// callers that cannot allocate device memory.  Every GPU that loads this
+// library holds the array (about 1.3 MB) until the process exits.
+namespace tmfg {
+
+constexpr size_t noalloc_round(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t kNoAllocBytes =
+    noalloc_round(4 * (size_t)TMFG_NOALLOC_MAX_N) +          // deg
+    noalloc_round(4 * ((size_t)TMFG_NOALLOC_MAX_N + 1)) +    // rowptr
+    noalloc_round(4 * (size_t)TMFG_NOALLOC_MAX_N) +          // cursor
+    noalloc_round(8 * 2 * (3 * (size_t)TMFG_NOALLOC_MAX_N - 6));  // arcs
+
+static __device__ __align__(256) unsigned char g_apsp_scratch[kNoAllocBytes];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoAllocMaxDevices];
+int g_noalloc_sms[kNoAllocMaxDevices];
+
+// Device address of the scratch array and the SM count of the current
+// device, looked up on the first call for that device.
+int noalloc_setup(void **ptr, int *sms)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+        cudaGetLastError();
+        return TMFG_ECUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        int s = 0;
+        if (cudaGetSymbolAddress(&p, g_apsp_scratch) != cudaSuccess || !p ||
+            cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return TMFG_ECUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+        g_noalloc_sms[dev] = s;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    *sms = g_noalloc_sms[dev];
+    return TMFG_OK;
+}
+}  // namespace
+
+}  // namespace tmfg
+
+extern "C" int tmfg_apsp_exact_noalloc(const void *S, int64_t n, int64_t ld, int32_t dtype,
+                                       const int32_t *edges, float *D, int64_t ldd,
+                                       int32_t *status, void *stream)
+{
+    using namespace tmfg;
+    if (!S || !edges || !D || !status || n < 4 || ld < n || ldd < n) return TMFG_EINVAL;
+    if (dtype != TMFG_F32 && dtype != TMFG_F64) return TMFG_EINVAL;
+    if (n > TMFG_NOALLOC_MAX_N || sssp_smem_bytes((int)n) > kSmemLimit) return TMFG_ETOOBIG;
+    void *work = nullptr;
+    int sms = 0;
+    int rc = noalloc_setup(&work, &sms);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the status output starts at zero; the degree counts are cleared by
+    // launch_apsp itself before they are accumulated
+    if (cudaMemsetAsync(status, 0, sizeof(int32_t), st) != cudaSuccess) return TMFG_ECUDA;
+    return launch_apsp(S, (int)n, ld, dtype, edges, 0, 0, 0.0f, D, ldd, work, status, sms,
+                       60ull * 1000000000ull, st);
+}

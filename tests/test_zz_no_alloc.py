@@ -1,0 +1,74 @@
+"""The allocation-free exact APSP entry point, tmfg_apsp_exact_noalloc.
+
+It exists for callers that cannot allocate device memory (their device
+memory belongs to their own pool or caching allocator, or the calling path
+must not take an allocator's locks and synchronisation).  Its scratch is a
+static device array shared by all calls, so this test calls it twice in a
+row, with different n, and checks each result bit for bit against the
+context-based tmfg_apsp, the tolerance the APSP parity tests use.  It also
+checks the size limit.  Collected last so that a failure here comes after
+every other test has run; it also passes alone in a fresh process.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2408_09399_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_09399_gb300 import build
+    build.build()
+    import paper_2408_09399_gb300 as T
+    lib = T.load_library()
+    P = ctypes.c_void_p
+    lib.tmfg_apsp_exact_noalloc.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, P,
+                                            P, ctypes.c_int64, P, P]
+    lib.tmfg_apsp_exact_noalloc.restype = ctypes.c_int
+    return T
+
+
+def noalloc(T, S, edges, D, status):
+    stream = torch.cuda.current_stream()
+    dt = 0 if S.dtype == torch.float32 else 1
+    return T.load_library().tmfg_apsp_exact_noalloc(
+        ctypes.c_void_p(S.data_ptr()), S.shape[0], S.stride(0), dt,
+        ctypes.c_void_p(edges.data_ptr()), ctypes.c_void_p(D.data_ptr()), D.stride(0),
+        ctypes.c_void_p(status.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+
+
+def test_noalloc_matches_context_entry_point_twice(T):
+    ctx = T.tmfg_create(0)
+    status = torch.full((1,), -7, dtype=torch.int32, device="cuda:0")
+    for n, dtype, seed in [(1500, np.float32, 1), (700, np.float64, 2)]:
+        S = torch.as_tensor(W.random_similarity(seed, n, dtype), device="cuda:0")
+        edges = T.tmfg_build(ctx, S, "heap")["edges"]
+        ref = T.tmfg_apsp(ctx, S, edges)
+        T.tmfg_sync_status(ctx)
+        D = torch.full((n, n), float("nan"), dtype=torch.float32, device="cuda:0")
+        assert noalloc(T, S, edges, D, status) == 0
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        assert torch.equal(D, ref), f"n={n}"
+    ctx.close()
+
+
+def test_noalloc_rejects_sizes_beyond_the_limit(T):
+    n = 21582  # TMFG_NOALLOC_MAX_N + 1
+    S = torch.zeros((4, 4), dtype=torch.float32, device="cuda:0")
+    edges = torch.zeros((6, 2), dtype=torch.int32, device="cuda:0")
+    D = torch.zeros((4, 4), dtype=torch.float32, device="cuda:0")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda:0")
+    lib = T.load_library()
+    rc = lib.tmfg_apsp_exact_noalloc(ctypes.c_void_p(S.data_ptr()), n, n, 0,
+                                     ctypes.c_void_p(edges.data_ptr()),
+                                     ctypes.c_void_p(D.data_ptr()), n,
+                                     ctypes.c_void_p(status.data_ptr()), None)
+    assert rc == 8  # TMFG_ETOOBIG, returned before any device work

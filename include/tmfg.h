@@ -165,7 +165,11 @@ int tmfg_sync_status(tmfg_ctx *ctx, void *stream);
 /* Counters of the last tmfg_build, valid after tmfg_sync_status:
  * out[0] = face evaluations, out[1] = stale heap pops, out[2] = pointer
  * scan chunks loaded, out[3] = insertion rounds, out[4] = loop time in ns
- * (device clock).  `count` <= 8 entries are written. */
+ * (device clock), out[5..7] = SM cycles spent recomputing faces, updating
+ * the max indexes, and selecting pairs (heap: resolving the stale pops);
+ * out[8..15] = a finer split of those cycles (push, refresh, gains,
+ * extraction, validation, resolution, stale scan) and the number of epoch
+ * iterations.  `count` <= 16 entries are written. */
 int tmfg_last_stats(tmfg_ctx *ctx, int64_t *out, int count);
 
 /* Static description of a return code. */

@@ -236,9 +236,12 @@ def tmfg_sync_status(ctx: Context, stream=None, raise_on_error: bool = True) -> 
 
 
 def tmfg_last_stats(ctx: Context) -> dict:
-    arr = (ctypes.c_int64 * 8)()
-    _check(load_library().tmfg_last_stats(ctx.handle, arr, 8), "tmfg_last_stats")
-    keys = ["face_evals", "stale_pops", "scan_chunks", "rounds", "loop_ns"]
+    arr = (ctypes.c_int64 * 16)()
+    _check(load_library().tmfg_last_stats(ctx.handle, arr, 16), "tmfg_last_stats")
+    keys = ["face_evals", "stale_pops", "scan_chunks", "rounds", "loop_ns", "cycles_recompute",
+            "cycles_index", "cycles_select", "cycles_push", "cycles_refresh", "cycles_gains",
+            "cycles_extract", "cycles_validate", "cycles_resolve", "cycles_stale_scan",
+            "epoch_iters"]
     return {k: int(arr[i]) for i, k in enumerate(keys)}
 
 

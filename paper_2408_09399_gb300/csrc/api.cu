@@ -48,7 +48,7 @@ struct tmfg_ctx {
     size_t work_bytes;
     int *status;        // device word
     long long *stats;   // device [8]
-    long long host_stats[8];
+    long long host_stats[16];
     unsigned long long timeout_ns;
 };
 
@@ -96,16 +96,18 @@ struct BuildWork {
     uint16_t *idx;
     long long *rowsum;
     int4 *face;
-    unsigned long long *leaf_gk;
-    int *leaf_v;
+    void *leaf_fresh, *leaf_stale, *pend_key;
+    unsigned long long *pend_cand;
     int *fu_buf;
+    void *state;
 };
 
 size_t build_work_bytes(int64_t n)
 {
     const size_t nf = 2 * (size_t)n - 4;
     return round256(2 * (size_t)n * (size_t)ldi_for(n)) + round256(8 * (size_t)n) +
-           round256(16 * nf) + round256(8 * nf) + round256(4 * nf) + round256(4 * nf);
+           round256(16 * nf) + 3 * round256(16 * nf) + round256(8 * nf) + round256(4 * nf) +
+           round256(loop_state_bytes((int)n));
 }
 
 BuildWork build_carve(void *base, int64_t n)
@@ -117,9 +119,12 @@ BuildWork build_carve(void *base, int64_t n)
     w.idx = static_cast<uint16_t *>(take(2 * (size_t)n * (size_t)ldi_for(n)));
     w.rowsum = static_cast<long long *>(take(8 * (size_t)n));
     w.face = static_cast<int4 *>(take(16 * nf));
-    w.leaf_gk = static_cast<unsigned long long *>(take(8 * nf));
-    w.leaf_v = static_cast<int *>(take(4 * nf));
+    w.leaf_fresh = take(16 * nf);
+    w.leaf_stale = take(16 * nf);
+    w.pend_key = take(16 * nf);
+    w.pend_cand = static_cast<unsigned long long *>(take(8 * nf));
     w.fu_buf = static_cast<int *>(take(4 * nf));
+    w.state = take(loop_state_bytes((int)n));
     return w;
 }
 
@@ -196,7 +201,9 @@ int64_t tmfg_max_n(int dtype)
 {
     if (dtype != TMFG_F32 && dtype != TMFG_F64) return 0;
     int64_t m = rowsort_max_n(dtype);
-    while (m > 4 && (loop_smem_bytes((int)m) > kSmemLimit || sssp_smem_bytes((int)m) > kSmemLimit))
+    while (m > 4 && (loop_smem_bytes((int)m, dtype, TMFG_HEAP) > kSmemLimit ||
+                      loop_smem_bytes((int)m, dtype, TMFG_CORR) > kSmemLimit ||
+                      sssp_smem_bytes((int)m) > kSmemLimit || 2 * m - 4 > 65535))
         --m;
     return m;
 }
@@ -261,9 +268,12 @@ int tmfg_build(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, const tmfg_p
     a.ins_face = ins_face;
     a.parent = bubble_parent;
     a.face = w.face;
-    a.leaf_gk = w.leaf_gk;
-    a.leaf_v = w.leaf_v;
+    a.leaf_fresh = w.leaf_fresh;
+    a.leaf_stale = w.leaf_stale;
+    a.pend_key = w.pend_key;
+    a.pend_cand = w.pend_cand;
     a.fu_buf = w.fu_buf;
+    a.state = w.state;
     a.status = ctx->status;
     a.stats = ctx->stats;
     a.timeout_ns = ctx->timeout_ns;
@@ -312,7 +322,7 @@ int tmfg_sync_status(tmfg_ctx *ctx, void *stream)
 int tmfg_last_stats(tmfg_ctx *ctx, int64_t *out, int count)
 {
     if (!ctx || !out || count < 0) return TMFG_EINVAL;
-    for (int i = 0; i < count && i < 8; ++i) out[i] = ctx->host_stats[i];
+    for (int i = 0; i < count && i < 16; ++i) out[i] = ctx->host_stats[i];
     return TMFG_OK;
 }
 

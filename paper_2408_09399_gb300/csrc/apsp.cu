@@ -28,7 +28,7 @@
 
 namespace tmfg {
 
-constexpr int kSsspThreads = 1024;
+constexpr int kSsspThreads = 512;
 
 // ------------------------------------------------------------------ CSR
 __global__ void csr_degree_kernel(const int *__restrict__ edges, int ne, int n, int *deg,
@@ -134,17 +134,25 @@ struct SsspArgs {
     unsigned long long timeout_ns;
 };
 
+// Shared memory: dist[n] floats, two frontier bitmaps, a frontier list of at
+// most list_cap ids, and a list of high-degree frontier vertices.
+__host__ __device__ inline int sssp_list_cap(int n) { return ((n / 2) + 15) & ~15; }
+constexpr int kHeavyCap = 512;
+constexpr int kHeavyDeg = 16;
+
 template <bool kBounded>
-__global__ void __launch_bounds__(kSsspThreads, 1) sssp_kernel(SsspArgs a)
+__global__ void __launch_bounds__(kSsspThreads, 2) sssp_kernel(SsspArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_cnt, s_abort;
-    const int n = a.n, tid = threadIdx.x;
+    __shared__ int s_cnt, s_listed, s_hcnt, s_abort, s_wnext;
+    const int n = a.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int W = (n + 31) / 32;
+    const int cap = sssp_list_cap(n);
     float *dist = reinterpret_cast<float *>(smem);
     uint32_t *bm0 = reinterpret_cast<uint32_t *>(smem + ((4 * (size_t)n + 15) & ~size_t(15)));
     uint32_t *bm1 = bm0 + W;
     uint16_t *list = reinterpret_cast<uint16_t *>(bm1 + W);
+    uint16_t *heavy = list + cap;
     const uint64_t t0 = globaltimer_ns();
 
     for (int i = blockIdx.x; i < a.nsrc; i += gridDim.x) {
@@ -165,46 +173,97 @@ __global__ void __launch_bounds__(kSsspThreads, 1) sssp_kernel(SsspArgs a)
         }
         uint32_t *cur = bm0, *nxt = bm1;
         __syncthreads();
-        for (int iter = 0; iter <= n + 1; ++iter) {
-            if (tid == 0) s_cnt = 0;
-            __syncthreads();
-            for (int w = tid; w < W; w += kSsspThreads) {
-                uint32_t b = cur[w];
-                if (b) {
+        int rounds = 0;
+        for (;;) {
+            // one Bellman-Ford round over the frontier in cur, in windows of
+            // at most cap frontier vertices
+            int wstart = 0;
+            bool any = false;
+            while (wstart < W) {
+                if (tid == 0) { s_cnt = 0; s_listed = 0; s_hcnt = 0; s_wnext = W; }
+                __syncthreads();
+                for (int w = wstart + tid; w < W; w += kSsspThreads) {
+                    uint32_t b = cur[w];
+                    if (!b) continue;
+                    const int c = __popc(b);
+                    const int pos = atomicAdd(&s_cnt, c);
+                    if (pos + c > cap) {  // the window is full: resume from this word
+                        atomicMin(&s_wnext, w);
+                        continue;
+                    }
                     cur[w] = 0;
-                    int pos = atomicAdd(&s_cnt, __popc(b));
+                    atomicAdd(&s_listed, c);
+                    int q = pos;
                     while (b) {
                         const int bit = __ffs(b) - 1;
                         b &= b - 1;
-                        list[pos++] = (uint16_t)(w * 32 + bit);
+                        list[q++] = (uint16_t)(w * 32 + bit);
                     }
                 }
+                __syncthreads();
+                // successful reservations form the prefix [0, s_listed); a
+                // word that did not fit stays set and starts the next window
+                const int cnt = s_listed;
+                const int wn = s_wnext;
+                any |= cnt > 0;
+                // relax: light vertices one per thread, heavy ones a warp each
+                for (int j = tid; j < cnt; j += kSsspThreads) {
+                    const int u = list[j];
+                    if (u >= n) continue;
+                    const float du = dist[u];
+                    if (kBounded && du > r) continue;
+                    const int p0 = a.rowptr[u], p1 = a.rowptr[u + 1];
+                    if (p1 - p0 > kHeavyDeg) {
+                        const int h = atomicAdd(&s_hcnt, 1);
+                        if (h < kHeavyCap) {
+                            heavy[h] = (uint16_t)u;
+                            continue;
+                        }
+                    }
+                    for (int p = p0; p < p1; p += 4) {
+                        uint2 arc[4];
+#pragma unroll
+                        for (int t = 0; t < 4; ++t)
+                            arc[t] = p + t < p1 ? a.arcs[p + t] : make_uint2(0xFFFFFFFFu, 0u);
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            const int w = (int)arc[t].x;
+                            if (w < 0 || w >= n) continue;
+                            const float nd = __fadd_rn(du, __uint_as_float(arc[t].y));
+                            if (nd < dist[w]) {
+                                const int old = atomicMin(reinterpret_cast<int *>(&dist[w]),
+                                                          __float_as_int(nd));
+                                if (__float_as_int(nd) < old) atomicOr(&nxt[w >> 5], 1u << (w & 31));
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+                const int hc = s_hcnt < kHeavyCap ? s_hcnt : kHeavyCap;
+                for (int j = warp; j < hc; j += kSsspThreads / 32) {
+                    const int u = heavy[j];
+                    const float du = dist[u];
+                    const int p1 = a.rowptr[u + 1];
+                    for (int p = a.rowptr[u] + lane; p < p1; p += 32) {
+                        const uint2 arc = a.arcs[p];
+                        const int w = (int)arc.x;
+                        const float nd = __fadd_rn(du, __uint_as_float(arc.y));
+                        if (nd < dist[w]) {
+                            const int old = atomicMin(reinterpret_cast<int *>(&dist[w]),
+                                                      __float_as_int(nd));
+                            if (__float_as_int(nd) < old) atomicOr(&nxt[w >> 5], 1u << (w & 31));
+                        }
+                    }
+                }
+                __syncthreads();
+                wstart = wn;
             }
-            __syncthreads();
-            const int cnt = s_cnt;
-            if (cnt == 0) break;
-            if (iter == n + 1) {  // cannot happen for a finite graph
+            if (!any) break;
+            uint32_t *t = cur; cur = nxt; nxt = t;
+            if (++rounds > n + 1) {  // cannot happen for a finite graph
                 if (tid == 0) set_status(a.status, TMFG_EINTERNAL);
                 break;
             }
-            const int g = tid >> 3, gl = tid & 7;
-            for (int j = g; j < cnt; j += kSsspThreads / 8) {
-                const int u = list[j];
-                const float du = dist[u];
-                if (kBounded && du > r) continue;
-                const int p1 = a.rowptr[u + 1];
-                for (int p = a.rowptr[u] + gl; p < p1; p += 8) {
-                    const uint2 arc = a.arcs[p];
-                    const int w = (int)arc.x;
-                    const float nd = __fadd_rn(du, __uint_as_float(arc.y));
-                    if (nd < dist[w]) {
-                        const int old = atomicMin(reinterpret_cast<int *>(&dist[w]), __float_as_int(nd));
-                        if (__float_as_int(nd) < old) atomicOr(&nxt[w >> 5], 1u << (w & 31));
-                    }
-                }
-            }
-            __syncthreads();
-            uint32_t *t = cur; cur = nxt; nxt = t;
         }
         // write the row
         float *orow = a.out + (long long)i * a.ldo;
@@ -238,7 +297,8 @@ __global__ void __launch_bounds__(kSsspThreads, 1) sssp_kernel(SsspArgs a)
 size_t sssp_smem_bytes(int n)
 {
     const size_t W = (n + 31) / 32;
-    return ((4 * (size_t)n + 15) & ~size_t(15)) + 8 * W + 2 * (size_t)n + 16;
+    return ((4 * (size_t)n + 15) & ~size_t(15)) + 8 * W + 2 * (size_t)sssp_list_cap(n) +
+           2 * (size_t)kHeavyCap + 16;
 }
 
 // ------------------------------------------------------------- hubs
@@ -439,7 +499,7 @@ int launch_apsp(const void *S, int n, long long ld, int dtype, const int *edges,
         a.nsrc = n;
         a.out = D;
         a.ldo = ldd;
-        const int grid = n < num_sms ? n : num_sms;
+        const int grid = n < 2 * num_sms ? n : 2 * num_sms;
         sssp_kernel<false><<<grid, kSsspThreads, smem, stream>>>(a);
         return cudaGetLastError() == cudaSuccess ? TMFG_OK : TMFG_ECUDA;
     }
@@ -454,7 +514,7 @@ int launch_apsp(const void *S, int n, long long ld, int dtype, const int *edges,
     a.nsrc = h;
     a.out = w.DH;
     a.ldo = n;
-    sssp_kernel<false><<<h < num_sms ? h : num_sms, kSsspThreads, smem, stream>>>(a);
+    sssp_kernel<false><<<h < 2 * num_sms ? h : 2 * num_sms, kSsspThreads, smem, stream>>>(a);
     nearest_hub_kernel<<<(n + 255) / 256, 256, 0, stream>>>(w.DH, h, n, w.near, w.dnear);
     // bounded search from every vertex, approximate rows, then min with the transpose
     a.src = nullptr;
@@ -465,7 +525,7 @@ int launch_apsp(const void *S, int n, long long ld, int dtype, const int *edges,
     a.near = w.near;
     a.DH = w.DH;
     a.rf = rf;
-    sssp_kernel<true><<<n < num_sms ? n : num_sms, kSsspThreads, smem, stream>>>(a);
+    sssp_kernel<true><<<n < 2 * num_sms ? n : 2 * num_sms, kSsspThreads, smem, stream>>>(a);
     const int T = (n + 31) / 32;
     sym_min_kernel<<<dim3(T, T), dim3(32, 8), 0, stream>>>(D, ldd, n);
     return cudaGetLastError() == cudaSuccess ? TMFG_OK : TMFG_ECUDA;

@@ -24,15 +24,21 @@ struct LoopArgs {
     int *edges;
     int *ins_face;
     int *parent;
-    int4 *face;                   // [2n-4] {a<b<c, owner bubble}
-    unsigned long long *leaf_gk;  // [2n-4] order-preserving gain key (0 = empty)
-    int *leaf_v;                  // [2n-4] stored best vertex
-    int *fu_buf;                  // [2n-4] corr-mode update list
+    int4 *face;                      // [2n-4] {a<b<c, owner bubble}
+    void *leaf_fresh;                // [2n-4] 16-byte slots: face keys, FRESH index
+    void *leaf_stale;                // [2n-4] 16-byte slots: face keys, STALE index (heap)
+    void *pend_key;                  // [2n-4] 16-byte slots: pending recomputed keys (heap)
+    unsigned long long *pend_cand;   // [2n-4] the 3 candidates a pending key used
+    int *fu_buf;                     // [2n-4] face update lists
     int *status;
-    long long *stats;             // [8]
+    long long *stats;             // [16]
     unsigned long long timeout_ns;
+    void *state;                  // loop state between segments (loop_state_bytes)
+    int k_stop;                   // a segment stops once k >= k_stop
+    int resume;                   // 0: first segment; 1: continue from state
 };
-size_t loop_smem_bytes(int n);
+size_t loop_smem_bytes(int n, int dtype, int mode);
+size_t loop_state_bytes(int n);
 int launch_loop(const LoopArgs &args, int dtype, cudaStream_t stream);
 
 // apsp.cu

@@ -2,32 +2,51 @@
 // prefix P, Algorithm 2 heap-tmfg), entirely on the device.
 //
 // One CTA runs the whole sequence of n-4 insertions with no host round trip.
-// State:
-//   shared  inserted bitmap, per-vertex lazy pointer ptr[w] into its sorted
-//           row and the cached MaxCorrs Mc[w] = row[w][ptr[w]] (16-bit ids),
-//           the stored best vertex fv[f] of each face, and a two-level max
-//           index over the face keys: level 1 = max of each group of 32
-//           faces, level 2 = max of each group of 32 level-1 nodes, then a
-//           root; dirty groups are recomputed after each batch of updates;
-//   global  the face triples and owners (int4), the per-face keys (leaves,
-//           L2-resident), the sorted rows (from the row sort) and S.
-// A face key is (gain desc, vertex asc, face id asc); with one entry per
-// face, popping the max of Algorithm 2's heap is the argmax over the faces'
-// stored keys, which is what the index returns.
 //
-// MaxCorrs[w] is read fresh (Algorithm 1 recomputes it for every vertex of
-// an updated face before reading it; Algorithm 2 likewise for the vertices
-// of the face it just popped or created): the cached Mc[w] is valid while it
-// is uninserted, else one warp scans row w from ptr[w]+1 with 16-byte loads
-// (256 entries per step) and a ballot over the inserted bitmap (the pointer
-// of Section 4.3, vectorised across a warp instead of AVX lanes).
+// Keys.  A face-vertex pair ranks by (gain desc, vertex asc, face id asc).
+// For float input the whole rank is one 64-bit word: the order-preserving
+// image of the gain in the high 32 bits, then 0xFFFF-vertex and 0xFFFF-face
+// (n <= 32770 keeps both in 16 bits), so a pair comparison is one unsigned
+// compare; for double input the gain image takes 64 bits and a second word
+// holds the rest.  Key 0 means "no pair".
 //
-// A face's best vertex is computed by one warp: 9 lanes gather S[x,u] for
-// the 3 candidates u x 3 face vertices x; gain = (S[a,u] + S[b,u]) + S[c,u]
-// with round-to-nearest adds in the dtype of S; ties go to the smaller u.
+// Max index.  For a set of faces, a two-level index: level 1 = max of each
+// group of 32 face keys (the keys themselves, the leaves, live in global
+// memory and stay in L2), level 2 = max of each group of 32 level-1 nodes,
+// then a root.  Writers mark the groups they touch; one batched update
+// recomputes the marked groups (a warp per group) and the root.
 //
-// The loop checks the device clock every iteration and stops with
-// TMFG_ETIMEOUT past its limit, so it always terminates.
+// MaxCorrs[w] is read fresh: the cached Mc[w] is kept while uninserted, else
+// one warp scans row w from ptr[w]+1 with 16-byte loads (256 sorted ids per
+// step) and a ballot over the inserted bitmap -- the lazily advanced pointer
+// of Section 4.3.  A face's best vertex is computed by one warp: 9 lanes
+// gather S[x,u] (3 candidates u x 3 face vertices x), gain = (S[a,u] +
+// S[b,u]) + S[c,u] with round-to-nearest adds in the dtype of S, ties to the
+// smaller u.
+//
+// corr-tmfg: one index over all faces.  A round takes the P best pairs
+// (repeated extraction), keeps the first pair of each vertex, inserts in
+// rank order, and recomputes F_update = {faces whose stored vertex was
+// inserted} + {new faces}.
+//
+// heap-tmfg: each face has exactly one heap entry, so Algorithm 2's pop is
+// the argmax over the faces' stored keys.  The faces are split between two
+// indexes: FRESH (stored vertex uninserted) and STALE (stored vertex
+// inserted).  After inserting v, the faces whose stored vertex is v move to
+// STALE keeping their (stale) keys, and their recomputation with the current
+// MaxCorrs is done at once, in parallel with the three new faces, and kept
+// as a pending result with the three candidates it used.  Algorithm 2 pops
+// stale faces in key order until the top of the heap is fresh; that epoch
+// is resolved in one batch: the stale faces ranking above the best fresh
+// key are extracted, sorted, and scanned in order -- a stale face is popped
+// while its stale key ranks above the running best, and its pending key
+// joins the running best.  A pending result is what a recompute at pop time
+// gives as long as its three candidates are still uninserted (the first
+// uninserted entry of a sorted row cannot change otherwise); if one was
+// inserted meanwhile, the face is recomputed before the scan.
+//
+// Every loop checks the device clock and stops with TMFG_ETIMEOUT past its
+// limit, so the kernel always terminates.
 #include <climits>
 
 #include "internal.cuh"
@@ -36,104 +55,202 @@ namespace tmfg {
 
 constexpr int kLoopThreads = 256;
 constexpr int kLoopWarps = kLoopThreads / kWarp;
-constexpr int kChunk = 256;    // faces per recompute batch
-constexpr int kMaxPrefix = 256;
+constexpr int kChunk = kLoopThreads;  // faces per recompute batch (one per thread)
+constexpr int kMaxPrefix = 256;  // largest corr-tmfg prefix
+constexpr int kXCap = 256;       // stale faces resolved in one batch
 
-struct Node {
-    unsigned long long gk;  // order-preserving image of the gain (0 = empty)
-    int v;
-    int f;
+// recompute destinations (encoded in bits 28..29 of a list entry)
+constexpr int kToFresh = 0;      // store as the face's key in the FRESH index
+constexpr int kToPendMove = 1;   // store as pending; move the face FRESH -> STALE
+constexpr int kToPend = 2;       // store as pending only
+
+// ------------------------------------------------------------------- keys
+template <typename T>
+struct KeyOps;
+
+template <>
+struct KeyOps<float> {
+    using Key = unsigned long long;
+    __device__ static Key empty() { return 0ull; }
+    __device__ static Key make(float g, int v, int f)
+    {
+        return ((Key)ord_key(g) << 32) | ((Key)(0xFFFFu - (unsigned)v) << 16) |
+               (Key)(0xFFFFu - (unsigned)f);
+    }
+    __device__ static bool gt(const Key &a, const Key &b) { return a > b; }
+    __device__ static bool is_empty(const Key &k) { return k == 0ull; }
+    __device__ static int vert(const Key &k) { return 0xFFFF - (int)((k >> 16) & 0xFFFFu); }
+    __device__ static int face(const Key &k) { return 0xFFFF - (int)(k & 0xFFFFu); }
+    __device__ static Key shfl_xor(const Key &k, int o) { return __shfl_xor_sync(0xffffffffu, k, o); }
 };
 
-__device__ __forceinline__ bool above(const Node &a, const Node &b)
-{
-    if (a.gk != b.gk) return a.gk > b.gk;
-    if (a.v != b.v) return a.v < b.v;
-    return a.f < b.f;
-}
+struct Key128 {
+    unsigned long long hi;  // order-preserving image of the double gain
+    unsigned long long lo;  // (0xFFFF - vertex) << 16 | (0xFFFF - face)
+};
 
-__device__ __forceinline__ Node node_empty() { return Node{0ull, INT_MAX, INT_MAX}; }
+template <>
+struct KeyOps<double> {
+    using Key = Key128;
+    __device__ static Key empty() { return Key128{0ull, 0ull}; }
+    __device__ static Key make(double g, int v, int f)
+    {
+        return Key128{ord_key(g), ((unsigned long long)(0xFFFFu - (unsigned)v) << 16) |
+                                      (unsigned long long)(0xFFFFu - (unsigned)f)};
+    }
+    __device__ static bool gt(const Key &a, const Key &b)
+    {
+        return a.hi != b.hi ? a.hi > b.hi : a.lo > b.lo;
+    }
+    __device__ static bool is_empty(const Key &k) { return k.hi == 0ull; }
+    __device__ static int vert(const Key &k) { return 0xFFFF - (int)((k.lo >> 16) & 0xFFFFu); }
+    __device__ static int face(const Key &k) { return 0xFFFF - (int)(k.lo & 0xFFFFu); }
+    __device__ static Key shfl_xor(const Key &k, int o)
+    {
+        return Key128{__shfl_xor_sync(0xffffffffu, k.hi, o), __shfl_xor_sync(0xffffffffu, k.lo, o)};
+    }
+};
 
-__device__ __forceinline__ Node warp_max(Node x)
+template <class KO>
+__device__ __forceinline__ typename KO::Key warp_max(typename KO::Key x)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        Node y;
-        y.gk = __shfl_xor_sync(0xffffffffu, x.gk, o);
-        y.v = __shfl_xor_sync(0xffffffffu, x.v, o);
-        y.f = __shfl_xor_sync(0xffffffffu, x.f, o);
-        if (above(y, x)) x = y;
+        const typename KO::Key y = KO::shfl_xor(x, o);
+        if (KO::gt(y, x)) x = y;
     }
     return x;
 }
 
+// ------------------------------------------------------------- max index
+template <class KO>
+struct Tree {
+    using Key = typename KO::Key;
+    Key *leaf;         // global [nfmax]
+    Key *l1, *l2;      // shared [G1], [G2]
+    uint32_t *b1, *b2; // dirty bits
+    uint16_t *q1, *q2; // dirty lists
+    int *n1, *n2;      // dirty counts (shared scalars)
+    Key *root;         // shared scalar
+
+    __device__ void mark(int f)
+    {
+        const int g = f >> 5;
+        const uint32_t bit = 1u << (g & 31);
+        if (!(atomicOr(&b1[g >> 5], bit) & bit)) q1[atomicAdd(n1, 1)] = (uint16_t)g;
+    }
+    __device__ void set(int f, const Key &k)
+    {
+        leaf[f] = k;
+        mark(f);
+    }
+};
+
 // Shared-memory layout (dynamic part), computed identically on the host.
 struct LoopLayout {
-    int W;      // words of an n-bit bitmap
-    int nfmax;  // 2n-4
-    int G1, G2; // level-1 / level-2 node counts
-    size_t off_ins, off_vmark, off_round, off_mc, off_ptr, off_fv, off_l1, off_l2, off_d1bits,
-        off_d2bits, off_d1list, off_d2list, off_vlist, off_flist, off_sel, total;
+    int W, nfmax, G1, G2;
+    size_t off_ins, off_vmark, off_rnd, off_mc, off_ptr, off_fv, off_tree[2], off_vlist, off_vslow,
+        off_sel, off_x, off_xkey, off_xpend, off_xs, off_q1x, off_q2x, total;
+    size_t tree_bytes;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-__host__ __device__ inline LoopLayout loop_layout(int n)
+// Per index: l1 [G1] keys, l2 [G2] keys, b1, b2 bits, q1 [G1], q2 [G2].
+__host__ __device__ inline size_t tree_layout_bytes(int G1, int G2, size_t ks)
+{
+    size_t o = 0;
+    o = align16(o + ks * (size_t)G1);
+    o = align16(o + ks * (size_t)G2);
+    o = align16(o + 4 * (size_t)((G1 + 31) / 32));
+    o = align16(o + 4 * (size_t)((G2 + 31) / 32));
+    o = align16(o + 2 * (size_t)G1);
+    o = align16(o + 2 * (size_t)G2);
+    return o;
+}
+
+__host__ __device__ inline LoopLayout loop_layout(int n, size_t ks, int ntrees)
 {
     LoopLayout L;
     L.W = (n + 31) / 32;
     L.nfmax = 2 * n - 4;
     L.G1 = (L.nfmax + 31) / 32;
     L.G2 = (L.G1 + 31) / 32;
+    L.tree_bytes = tree_layout_bytes(L.G1, L.G2, ks);
     size_t o = 0;
-    L.off_ins = o;    o = align16(o + 4 * (size_t)L.W);
-    L.off_vmark = o;  o = align16(o + 4 * (size_t)L.W);
-    L.off_round = o;  o = align16(o + 4 * (size_t)L.W);
-    L.off_mc = o;     o = align16(o + 2 * (size_t)n);
-    L.off_ptr = o;    o = align16(o + 2 * (size_t)n);
-    L.off_fv = o;     o = align16(o + 2 * (size_t)L.nfmax);
-    L.off_l1 = o;     o = align16(o + sizeof(Node) * (size_t)L.G1);
-    L.off_l2 = o;     o = align16(o + sizeof(Node) * (size_t)L.G2);
-    L.off_d1bits = o; o = align16(o + 4 * (size_t)((L.G1 + 31) / 32));
-    L.off_d2bits = o; o = align16(o + 4 * (size_t)((L.G2 + 31) / 32));
-    L.off_d1list = o; o = align16(o + 2 * (size_t)L.G1);
-    L.off_d2list = o; o = align16(o + 2 * (size_t)L.G2);
-    L.off_vlist = o;  o = align16(o + 4 * (size_t)(3 * kChunk));
-    L.off_flist = o;  o = align16(o + 4 * (size_t)4);
-    L.off_sel = o;    o = align16(o + sizeof(Node) * (size_t)kMaxPrefix);
+    L.off_ins = o;   o = align16(o + 4 * (size_t)L.W);
+    L.off_vmark = o; o = align16(o + 4 * (size_t)L.W);
+    L.off_rnd = o;   o = align16(o + 4 * (size_t)L.W);
+    L.off_mc = o;    o = align16(o + 2 * (size_t)n);
+    L.off_ptr = o;   o = align16(o + 2 * (size_t)n);
+    L.off_fv = o;    o = align16(o + 2 * (size_t)L.nfmax);
+    L.off_tree[0] = o; o += L.tree_bytes;
+    L.off_tree[1] = o; o += ntrees > 1 ? L.tree_bytes : 0;
+    L.off_vlist = o; o = align16(o + 4 * (size_t)(3 * kChunk));
+    L.off_vslow = o; o = align16(o + 4 * (size_t)(3 * kChunk));
+    L.off_sel = o;   o = align16(o + ks * (size_t)kMaxPrefix);
+    L.off_x = o;     o = align16(o + 4 * (size_t)kXCap);
+    L.off_xkey = o;  o = align16(o + ks * (size_t)kXCap);
+    L.off_xpend = o; o = align16(o + ks * (size_t)kXCap);
+    L.off_xs = o;    o = align16(o + 2 * (size_t)kXCap);
+    L.off_q1x = o;   o = align16(o + 2 * (size_t)L.G1);
+    L.off_q2x = o;   o = align16(o + 2 * (size_t)64);
     L.total = o;
     return L;
 }
 
+// Loop state kept in global memory between segments of the loop (the rows
+// are compacted between segments): scalars, then the shared arrays.
+struct StateLayout {
+    size_t off_scal, off_roots, off_ins, off_mc, off_ptr, off_fv, off_tree[2], total;
+};
+
+__host__ __device__ inline StateLayout state_layout(int n, size_t ks)
+{
+    const LoopLayout L = loop_layout(n, ks, 2);
+    StateLayout S;
+    size_t o = 0;
+    S.off_scal = o;  o = align16(o + 8 * 32);
+    S.off_roots = o; o = align16(o + 2 * ks);
+    S.off_ins = o;   o = align16(o + 4 * (size_t)L.W);
+    S.off_mc = o;    o = align16(o + 2 * (size_t)n);
+    S.off_ptr = o;   o = align16(o + 2 * (size_t)n);
+    S.off_fv = o;    o = align16(o + 2 * (size_t)L.nfmax);
+    for (int t = 0; t < 2; ++t) {
+        S.off_tree[t] = o;
+        o = align16(o + ks * (size_t)(L.G1 + L.G2));
+    }
+    S.total = o;
+    return S;
+}
+
+size_t loop_state_bytes(int n) { return state_layout(n, sizeof(Key128)).total; }
+
 template <typename T>
 struct Loop {
+    using KO = KeyOps<T>;
+    using Key = typename KO::Key;
     const LoopArgs &a;
     const T *S;
-    int n;
-    uint32_t *ins, *vmark, *rnd, *d1bits, *d2bits;
-    uint16_t *mc, *ptr, *fv, *d1list, *d2list;
-    Node *l1, *l2, *sel;
-    int *vlist, *flist;
-    int G1, G2;
-    // scalars (static shared)
-    Node *root;
-    int *nf, *k, *vcount, *nd1, *nd2, *scan_chunks, *face_evals;
+    int n, nfmax, G1, G2;
+    uint32_t *ins, *vmark, *rnd;
+    uint16_t *mc, *ptr, *fv;
+    Tree<KO> tf, ts;  // FRESH (all faces in corr mode), STALE (heap mode)
+    int *vlist, *vslowlist;
+    Key *sel, *xkey, *xpend;
+    int *xf;
+    uint16_t *xs, *q1x, *q2x;
+    Key *pend_key;
+    unsigned long long *pend_cand;
+    // shared scalars
+    int *nf, *k, *vcount, *vslow, *scan_chunks, *face_evals;
+    long long cyc_push = 0, cyc_refresh = 0, cyc_gain = 0;  // thread 0's view
 
     __device__ bool is_ins(int v) const { return (ins[v >> 5] >> (v & 31)) & 1u; }
 
-    __device__ void mark_d1(int g)
-    {
-        const uint32_t bit = 1u << (g & 31);
-        if (!(atomicOr(&d1bits[g >> 5], bit) & bit)) d1list[atomicAdd(nd1, 1)] = (uint16_t)g;
-    }
-    __device__ void mark_d2(int g)
-    {
-        const uint32_t bit = 1u << (g & 31);
-        if (!(atomicOr(&d2bits[g >> 5], bit) & bit)) d2list[atomicAdd(nd2, 1)] = (uint16_t)g;
-    }
-
     // Fresh MaxCorrs of vertex w (one warp): keep Mc[w] while uninserted,
-    // else advance ptr[w] to the first uninserted entry of row w.
+    // else advance ptr[w] to the first uninserted entry of row w.  An id
+    // >= n (0xFFFF) ends the row.
     __device__ void refresh(int w)
     {
         const int lane = threadIdx.x & 31;
@@ -151,25 +268,31 @@ struct Loop {
                 const uint4 c = *reinterpret_cast<const uint4 *>(row + q0);
                 e[0] = c.x & 0xFFFF; e[1] = c.x >> 16; e[2] = c.y & 0xFFFF; e[3] = c.y >> 16;
                 e[4] = c.z & 0xFFFF; e[5] = c.z >> 16; e[6] = c.w & 0xFFFF; e[7] = c.w >> 16;
+            }
 #pragma unroll
-                for (int t = 7; t >= 0; --t) {
-                    const int q = q0 + t;
-                    if (q >= p && q < mlen && e[t] < n && !is_ins(e[t])) first = t;
-                }
+            for (int t = 7; t >= 0; --t) {
+                const int q = q0 + t;
+                if (q >= p && (q >= mlen || e[t] >= n || !is_ins(e[t]))) first = t;
             }
             if (lane == 0) atomicAdd(scan_chunks, 1);
             const unsigned bal = __ballot_sync(0xffffffffu, first < 8);
             if (bal) {
                 const int src = __ffs(bal) - 1;
                 const int t = __shfl_sync(0xffffffffu, first, src);
-                uint16_t hit = 0;
+                int hit = kNone16;
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
                     if (u == t) hit = e[u];
-                hit = (uint16_t)__shfl_sync(0xffffffffu, (int)hit, src);
+                hit = __shfl_sync(0xffffffffu, hit, src);
+                const int q = base + src * 8 + t;
                 if (lane == 0) {
-                    ptr[w] = (uint16_t)(base + src * 8 + t);
-                    mc[w] = hit;
+                    if (q < mlen && hit < n) {
+                        ptr[w] = (uint16_t)q;
+                        mc[w] = (uint16_t)hit;
+                    } else {
+                        ptr[w] = (uint16_t)(q < mlen ? q : mlen);
+                        mc[w] = kNone16;
+                    }
                 }
                 __syncwarp();
                 return;
@@ -183,59 +306,108 @@ struct Loop {
         __syncwarp();
     }
 
-    // Best vertex of face f from the fresh MaxCorrs of its vertices (one warp).
-    __device__ void face_best(int f)
+    // One thread's first look for the fresh MaxCorrs of w: the 16 sorted ids
+    // after ptr[w] (two 16-byte loads).  Returns false if w still needs the
+    // warp-wide scan.
+    __device__ bool refresh_probe(int w)
     {
-        const int lane = threadIdx.x & 31;
-        const int4 fc = a.face[f];
-        const int m0 = mc[fc.x], m1 = mc[fc.y], m2 = mc[fc.z];
-        const int ci = lane / 3, cj = lane - 3 * (lane / 3);
-        T val = T(0);
-        if (lane < 9) {
-            const int cand = ci == 0 ? m0 : (ci == 1 ? m1 : m2);
-            const int fx = cj == 0 ? fc.x : (cj == 1 ? fc.y : fc.z);
-            if (cand != kNone16 && cand < n) val = canon(S[(long long)fx * a.ld + cand]);
+        const uint16_t m = mc[w];
+        if (m == kNone16 || !is_ins(m)) return true;
+        const int mlen = n - 1;
+        const int p = ptr[w] + 1;
+        if (p >= mlen) {
+            ptr[w] = (uint16_t)mlen;
+            mc[w] = kNone16;
+            return true;
         }
-        const int l3 = (3 * lane) & 31;
-        const T x0 = shfl(val, l3), x1 = shfl(val, (l3 + 1) & 31), x2 = shfl(val, (l3 + 2) & 31);
-        const T g = canon(add_rn(add_rn(x0, x1), x2));
-        const T g1 = shfl(g, 1), g2 = shfl(g, 2);
-        if (lane == 0) {
-            int bv = -1;
-            T bg = T(0);
-            const int cs[3] = {m0, m1, m2};
-            const T gs[3] = {g, g1, g2};
+        const uint16_t *row = a.idx + (long long)w * a.ldi;
+        const int base = p & ~7;
+        uint4 c[2];
+        c[0] = *reinterpret_cast<const uint4 *>(row + base);
+        c[1] = base + 8 < a.ldi ? *reinterpret_cast<const uint4 *>(row + base + 8)
+                                : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+        atomicAdd(scan_chunks, 1);
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const int c = cs[i];
-                if (c == kNone16 || c >= n) continue;
-                if (bv < 0 || gs[i] > bg || (gs[i] == bg && c < bv)) { bv = c; bg = gs[i]; }
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t wd[4] = {c[h].x, c[h].y, c[h].z, c[h].w};
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int q = base + 8 * h + t;
+                const int e = (wd[t >> 1] >> (16 * (t & 1))) & 0xFFFF;
+                if (q < p) continue;
+                if (q >= mlen || e >= n) {  // end of the row
+                    ptr[w] = (uint16_t)(q < mlen ? q : mlen);
+                    mc[w] = kNone16;
+                    return true;
+                }
+                if (!is_ins(e)) {
+                    ptr[w] = (uint16_t)q;
+                    mc[w] = (uint16_t)e;
+                    return true;
+                }
             }
-            if (bv < 0) {
-                a.leaf_gk[f] = 0ull;
-                a.leaf_v[f] = INT_MAX;
-                fv[f] = kNone16;
-            } else {
-                a.leaf_gk[f] = (unsigned long long)ord_key(bg);
-                a.leaf_v[f] = bv;
-                fv[f] = (uint16_t)bv;
-            }
-            atomicAdd(face_evals, 1);
-            mark_d1(f >> 5);
         }
-        __syncwarp();
+        ptr[w] = (uint16_t)(base + 15);  // all inserted up to here (base + 15 < mlen)
+        return false;
     }
 
-    // Recompute the faces of list[0..cnt) (list in shared or global memory).
+    // Best vertex of face f = {fc.x < fc.y < fc.z} from the fresh MaxCorrs of
+    // its vertices (one thread: 9 independent gathers), stored per dest.
+    __device__ void face_best_thread(int f, int4 fc, int dest)
+    {
+        const int cs[3] = {mc[fc.x], mc[fc.y], mc[fc.z]};
+        const int xs[3] = {fc.x, fc.y, fc.z};
+        Key old = KO::empty();
+        if (dest == kToPendMove) old = tf.leaf[f];
+        T v[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                v[i][j] = (cs[i] != kNone16 && cs[i] < n) ? S[(long long)xs[j] * a.ld + cs[i]] : T(0);
+        int bv = -1;
+        T bg = T(0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int c = cs[i];
+            if (c == kNone16 || c >= n) continue;
+            const T g = canon(add_rn(add_rn(canon(v[i][0]), canon(v[i][1])), canon(v[i][2])));
+            if (bv < 0 || g > bg || (g == bg && c < bv)) { bv = c; bg = g; }
+        }
+        const Key key = bv < 0 ? KO::empty() : KO::make(bg, bv, f);
+        if (dest == kToFresh) {
+            tf.set(f, key);
+            fv[f] = bv < 0 ? kNone16 : (uint16_t)bv;
+        } else {
+            pend_key[f] = key;
+            pend_cand[f] = (unsigned long long)(unsigned)cs[0] |
+                           ((unsigned long long)(unsigned)cs[1] << 16) |
+                           ((unsigned long long)(unsigned)cs[2] << 32);
+            if (dest == kToPendMove) {
+                ts.set(f, old);
+                tf.set(f, KO::empty());
+            }
+        }
+        atomicAdd(face_evals, 1);
+    }
+
+    // Recompute the faces of list[0..cnt): entry = face | dest << 28.  The
+    // list may be in shared or global memory.  One thread per face, one
+    // thread per vertex to refresh (a warp per vertex when the first 16
+    // sorted ids are all inserted).  Ends synchronised.
     __device__ void recompute(const int *list, int cnt)
     {
         const int tid = threadIdx.x, warp = tid >> 5;
         for (int c0 = 0; c0 < cnt; c0 += kChunk) {
             const int m = cnt - c0 < kChunk ? cnt - c0 : kChunk;
-            if (tid == 0) *vcount = 0;
+            long long c0t = clock64();
+            if (tid == 0) { *vcount = 0; *vslow = 0; }
             __syncthreads();
-            for (int i = tid; i < m; i += kLoopThreads) {
-                const int4 fc = a.face[list[c0 + i]];
+            int4 fc = make_int4(0, 0, 0, 0);
+            int fe = 0;
+            if (tid < m) {
+                fe = list[c0 + tid];
+                fc = a.face[fe & 0x0FFFFFFF];
                 const int vs[3] = {fc.x, fc.y, fc.z};
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
@@ -245,71 +417,97 @@ struct Loop {
                 }
             }
             __syncthreads();
+            long long c1t = clock64();
+            cyc_push += c1t - c0t;
             const int nv = *vcount;
-            for (int i = warp; i < nv; i += kLoopWarps) refresh(vlist[i]);
+            for (int i = tid; i < nv; i += kLoopThreads) {
+                const int w = vlist[i];
+                if (!refresh_probe(w)) vslowlist[atomicAdd(vslow, 1)] = w;
+            }
             __syncthreads();
+            const int ns = *vslow;
+            for (int i = warp; i < ns; i += kLoopWarps) refresh(vslowlist[i]);
+            __syncthreads();
+            long long c2t = clock64();
+            cyc_refresh += c2t - c1t;
             for (int i = tid; i < nv; i += kLoopThreads) {
                 const int w = vlist[i];
                 atomicAnd(&vmark[w >> 5], ~(1u << (w & 31)));
             }
-            for (int i = warp; i < m; i += kLoopWarps) face_best(list[c0 + i]);
+            if (tid < m) face_best_thread(fe & 0x0FFFFFFF, fc, (fe >> 28) & 3);
             __syncthreads();
+            cyc_gain += clock64() - c2t;
         }
     }
 
-    // Bring the max index up to date after leaf writes (ends synchronised).
-    __device__ void tree_update()
+    // Level-1 recompute of the marked groups of index x (warp per group).
+    __device__ void update_l1(Tree<KO> &x)
     {
-        const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-        const int nfc = *nf;
-        const int c1 = *nd1;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int c1 = *x.n1;
         for (int i = warp; i < c1; i += kLoopWarps) {
-            const int g = d1list[i];
+            const int g = x.q1[i];
             const int f = g * 32 + lane;
-            Node x = node_empty();
-            if (f < nfc) {
-                x.gk = a.leaf_gk[f];
-                x.v = a.leaf_v[f];
-                x.f = f;
-                if (x.gk == 0ull) x = node_empty();
-            }
-            x = warp_max(x);
+            Key v = f < nfmax ? x.leaf[f] : KO::empty();
+            v = warp_max<KO>(v);
             if (lane == 0) {
-                l1[g] = x;
-                atomicAnd(&d1bits[g >> 5], ~(1u << (g & 31)));
-                mark_d2(g >> 5);
+                x.l1[g] = v;
+                atomicAnd(&x.b1[g >> 5], ~(1u << (g & 31)));
+                const int g2 = g >> 5;
+                const uint32_t bit = 1u << (g2 & 31);
+                if (!(atomicOr(&x.b2[g2 >> 5], bit) & bit)) x.q2[atomicAdd(x.n2, 1)] = (uint16_t)g2;
             }
         }
-        __syncthreads();
-        const int c2 = *nd2;
+    }
+    __device__ void update_l2(Tree<KO> &x)
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int c2 = *x.n2;
         for (int i = warp; i < c2; i += kLoopWarps) {
-            const int g = d2list[i];
+            const int g = x.q2[i];
             const int j = g * 32 + lane;
-            Node x = j < G1 ? l1[j] : node_empty();
-            x = warp_max(x);
+            Key v = j < G1 ? x.l1[j] : KO::empty();
+            v = warp_max<KO>(v);
             if (lane == 0) {
-                l2[g] = x;
-                atomicAnd(&d2bits[g >> 5], ~(1u << (g & 31)));
+                x.l2[g] = v;
+                atomicAnd(&x.b2[g >> 5], ~(1u << (g & 31)));
             }
         }
+    }
+    __device__ void update_root(Tree<KO> &x)
+    {
+        const int lane = threadIdx.x & 31;
+        Key v = lane < G2 ? x.l2[lane] : KO::empty();
+        const Key y = lane + 32 < G2 ? x.l2[lane + 32] : KO::empty();
+        if (KO::gt(y, v)) v = y;
+        v = warp_max<KO>(v);
+        if (lane == 0) {
+            *x.root = v;
+            *x.n1 = 0;
+            *x.n2 = 0;
+        }
+    }
+
+    // Batched update of the marked groups of the FRESH index (and of the
+    // STALE index when both is set).  Starts and ends synchronised.
+    __device__ void update(int both)
+    {
+        const int warp = threadIdx.x >> 5;
         __syncthreads();
-        if (warp == 0) {
-            Node x = lane < G2 ? l2[lane] : node_empty();
-            Node y = lane + 32 < G2 ? l2[lane + 32] : node_empty();
-            if (above(y, x)) x = y;
-            x = warp_max(x);
-            if (lane == 0) {
-                *root = x;
-                *nd1 = 0;
-                *nd2 = 0;
-            }
-        }
+        update_l1(tf);
+        if (both) update_l1(ts);
+        __syncthreads();
+        update_l2(tf);
+        if (both) update_l2(ts);
+        __syncthreads();
+        if (warp == 0) update_root(tf);
+        if (both && warp == 1) update_root(ts);
         __syncthreads();
     }
 
-    // Thread 0 only: insert v into face f (Algorithm 1/2 insertion step);
-    // writes the outputs and the 3 new faces; returns their ids in out3.
-    __device__ void insert_pair(int v, int f, int *out3)
+    // Thread 0 only: insert v into face f; writes the outputs and the 3 new
+    // faces (slot f, then nf, nf+1).
+    __device__ void insert_pair(int v, int f)
     {
         const int4 fc = a.face[f];
         const int x = fc.x, y = fc.y, z = fc.z;
@@ -336,180 +534,417 @@ struct Loop {
         a.face[nfc + 1] = sorted(v, x, z);
         fv[nfc] = kNone16;
         fv[nfc + 1] = kNone16;
-        out3[0] = f;
-        out3[1] = nfc;
-        out3[2] = nfc + 1;
         *nf = nfc + 2;
         *k = kk + 1;
+    }
+
+    __device__ bool pend_valid(int f) const
+    {
+        const unsigned long long c = pend_cand[f];
+        if (KO::is_empty(pend_key[f])) return false;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int u = (int)((c >> (16 * i)) & 0xFFFFu);
+            if (u != kNone16 && (u >= n || is_ins(u))) return false;
+        }
+        return true;
     }
 };
 
 template <typename T>
 __global__ void __launch_bounds__(kLoopThreads, 1) tmfg_loop_kernel(LoopArgs a)
 {
+    using KO = KeyOps<T>;
+    using Key = typename KO::Key;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ Node s_root;
-    __shared__ int s_nf, s_k, s_vcount, s_nd1, s_nd2, s_scan, s_evals, s_stop, s_nsel, s_fcount;
+    __shared__ Key s_root[2], s_win;
+    __shared__ int s_n1[2], s_n2[2];
+    __shared__ int s_vslow;
+    __shared__ int s_nf, s_k, s_vcount, s_scan, s_evals, s_stop, s_nsel, s_fcount;
+    __shared__ int s_nx, s_ninv, s_nq1, s_nq2, s_np, s_more;
+    __shared__ Key s_tau;
     __shared__ int s_clique[4];
-    __shared__ unsigned long long s_red_r[kLoopWarps];
+    __shared__ long long s_red_r[kLoopWarps];
     __shared__ int s_red_i[kLoopWarps];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = a.n;
     if (*(volatile int *)a.status != 0) return;  // an earlier step failed
     const uint64_t t0 = globaltimer_ns();
-    const LoopLayout L = loop_layout(n);
+    const bool heap = a.mode == TMFG_HEAP;
+    const LoopLayout L = loop_layout(n, sizeof(Key), heap ? 2 : 1);
 
     Loop<T> st{a};
     st.S = reinterpret_cast<const T *>(a.S);
     st.n = n;
+    st.nfmax = L.nfmax;
+    st.G1 = L.G1;
+    st.G2 = L.G2;
     st.ins = reinterpret_cast<uint32_t *>(smem + L.off_ins);
     st.vmark = reinterpret_cast<uint32_t *>(smem + L.off_vmark);
-    st.rnd = reinterpret_cast<uint32_t *>(smem + L.off_round);
+    st.rnd = reinterpret_cast<uint32_t *>(smem + L.off_rnd);
     st.mc = reinterpret_cast<uint16_t *>(smem + L.off_mc);
     st.ptr = reinterpret_cast<uint16_t *>(smem + L.off_ptr);
     st.fv = reinterpret_cast<uint16_t *>(smem + L.off_fv);
-    st.l1 = reinterpret_cast<Node *>(smem + L.off_l1);
-    st.l2 = reinterpret_cast<Node *>(smem + L.off_l2);
-    st.d1bits = reinterpret_cast<uint32_t *>(smem + L.off_d1bits);
-    st.d2bits = reinterpret_cast<uint32_t *>(smem + L.off_d2bits);
-    st.d1list = reinterpret_cast<uint16_t *>(smem + L.off_d1list);
-    st.d2list = reinterpret_cast<uint16_t *>(smem + L.off_d2list);
+    auto bind = [&](Tree<KO> &x, int t, void *leaf) {
+        unsigned char *b = smem + L.off_tree[t];
+        size_t o = 0;
+        x.leaf = reinterpret_cast<Key *>(leaf);
+        x.l1 = reinterpret_cast<Key *>(b + o);      o = align16(o + sizeof(Key) * (size_t)L.G1);
+        x.l2 = reinterpret_cast<Key *>(b + o);      o = align16(o + sizeof(Key) * (size_t)L.G2);
+        x.b1 = reinterpret_cast<uint32_t *>(b + o); o = align16(o + 4 * (size_t)((L.G1 + 31) / 32));
+        x.b2 = reinterpret_cast<uint32_t *>(b + o); o = align16(o + 4 * (size_t)((L.G2 + 31) / 32));
+        x.q1 = reinterpret_cast<uint16_t *>(b + o); o = align16(o + 2 * (size_t)L.G1);
+        x.q2 = reinterpret_cast<uint16_t *>(b + o);
+        x.n1 = &s_n1[t];
+        x.n2 = &s_n2[t];
+        x.root = &s_root[t];
+    };
+    bind(st.tf, 0, a.leaf_fresh);
+    bind(st.ts, 1, a.leaf_stale);
     st.vlist = reinterpret_cast<int *>(smem + L.off_vlist);
-    st.flist = reinterpret_cast<int *>(smem + L.off_flist);
-    st.sel = reinterpret_cast<Node *>(smem + L.off_sel);
-    st.G1 = L.G1;
-    st.G2 = L.G2;
-    st.root = &s_root;
+    st.vslowlist = reinterpret_cast<int *>(smem + L.off_vslow);
+    st.sel = reinterpret_cast<Key *>(smem + L.off_sel);
+    st.xf = reinterpret_cast<int *>(smem + L.off_x);
+    st.xkey = reinterpret_cast<Key *>(smem + L.off_xkey);
+    st.xpend = reinterpret_cast<Key *>(smem + L.off_xpend);
+    st.xs = reinterpret_cast<uint16_t *>(smem + L.off_xs);
+    st.q1x = reinterpret_cast<uint16_t *>(smem + L.off_q1x);
+    st.q2x = reinterpret_cast<uint16_t *>(smem + L.off_q2x);
+    st.pend_key = reinterpret_cast<Key *>(a.pend_key);
+    st.pend_cand = a.pend_cand;
     st.nf = &s_nf;
     st.k = &s_k;
     st.vcount = &s_vcount;
-    st.nd1 = &s_nd1;
-    st.nd2 = &s_nd2;
+    st.vslow = &s_vslow;
     st.scan_chunks = &s_scan;
     st.face_evals = &s_evals;
 
-    // ---- initial state
-    for (int i = tid; i < L.W; i += kLoopThreads) { st.ins[i] = 0; st.vmark[i] = 0; st.rnd[i] = 0; }
-    for (int w = tid; w < n; w += kLoopThreads) {
-        st.ptr[w] = 0;
-        const uint16_t m0 = a.idx[(long long)w * a.ldi];
-        st.mc[w] = m0 < n ? m0 : kNone16;
-    }
-    for (int f = tid; f < L.nfmax; f += kLoopThreads) st.fv[f] = kNone16;
-    for (int g = tid; g < L.G1; g += kLoopThreads) st.l1[g] = node_empty();
-    for (int g = tid; g < L.G2; g += kLoopThreads) st.l2[g] = node_empty();
-    for (int i = tid; i < (L.G1 + 31) / 32; i += kLoopThreads) st.d1bits[i] = 0;
-    for (int i = tid; i < (L.G2 + 31) / 32; i += kLoopThreads) st.d2bits[i] = 0;
-    if (tid == 0) {
-        s_nf = 4; s_k = 0; s_vcount = 0; s_nd1 = 0; s_nd2 = 0; s_scan = 0; s_evals = 0;
-        s_stop = 0; s_nsel = 0; s_fcount = 0;
-    }
-    __syncthreads();
-
-    // ---- initial 4-clique: top four row sums (r desc, id asc)
-    for (int c = 0; c < 4; ++c) {
-        long long br = LLONG_MIN;
-        int bi = INT_MAX;
-        for (int v = tid; v < n; v += kLoopThreads) {
-            bool taken = false;
-            for (int j = 0; j < c; ++j) taken |= (s_clique[j] == v);
-            if (taken) continue;
-            const long long r = a.rowsum[v];
-            if (r > br || (r == br && v < bi)) { br = r; bi = v; }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const long long r2 = __shfl_xor_sync(0xffffffffu, br, o);
-            const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (r2 > br || (r2 == br && i2 < bi)) { br = r2; bi = i2; }
-        }
-        if (lane == 0) { s_red_r[warp] = (unsigned long long)br; s_red_i[warp] = bi; }
-        __syncthreads();
+    const StateLayout SL = state_layout(n, sizeof(Key128));
+    unsigned char *gs = reinterpret_cast<unsigned char *>(a.state);
+    long long *gscal = reinterpret_cast<long long *>(gs + SL.off_scal);
+    // stats carried across segments: 0 evals, 1 stale, 2 scan, 3 rounds, 4 ns,
+    // 5..14 cycle counters, 15 epoch iterations; 16 nf, 17 k
+    long long acc[16];
+    for (int i = 0; i < 16; ++i) acc[i] = 0;
+    if (a.resume) {
+        for (int i = 0; i < 16; ++i) acc[i] = gscal[i];
+        const uint32_t *gins = reinterpret_cast<const uint32_t *>(gs + SL.off_ins);
+        const uint16_t *gmc = reinterpret_cast<const uint16_t *>(gs + SL.off_mc);
+        const uint16_t *gptr = reinterpret_cast<const uint16_t *>(gs + SL.off_ptr);
+        const uint16_t *gfv = reinterpret_cast<const uint16_t *>(gs + SL.off_fv);
+        for (int i = tid; i < L.W; i += kLoopThreads) { st.ins[i] = gins[i]; st.vmark[i] = 0; st.rnd[i] = 0; }
+        for (int w = tid; w < n; w += kLoopThreads) { st.mc[w] = gmc[w]; st.ptr[w] = gptr[w]; }
+        for (int f = tid; f < L.nfmax; f += kLoopThreads) st.fv[f] = gfv[f];
+        auto load_tree = [&](Tree<KO> &x, int t) {
+            const Key *g = reinterpret_cast<const Key *>(gs + SL.off_tree[t]);
+            for (int i = tid; i < L.G1; i += kLoopThreads) x.l1[i] = g[i];
+            for (int i = tid; i < L.G2; i += kLoopThreads) x.l2[i] = g[L.G1 + i];
+            for (int i = tid; i < (L.G1 + 31) / 32; i += kLoopThreads) x.b1[i] = 0;
+            for (int i = tid; i < (L.G2 + 31) / 32; i += kLoopThreads) x.b2[i] = 0;
+        };
+        load_tree(st.tf, 0);
+        if (heap) load_tree(st.ts, 1);
         if (tid == 0) {
-            long long r = (long long)s_red_r[0];
-            int i = s_red_i[0];
-            for (int w = 1; w < kLoopWarps; ++w) {
-                const long long r2 = (long long)s_red_r[w];
-                const int i2 = s_red_i[w];
-                if (r2 > r || (r2 == r && i2 < i)) { r = r2; i = i2; }
-            }
-            s_clique[c] = i;
+            const Key *gr = reinterpret_cast<const Key *>(gs + SL.off_roots);
+            s_nf = (int)gscal[16]; s_k = (int)gscal[17];
+            s_vcount = 0; s_scan = 0; s_evals = 0; s_stop = 0; s_nsel = 0; s_fcount = 0;
+            s_n1[0] = s_n1[1] = s_n2[0] = s_n2[1] = 0;
+            s_root[0] = gr[0];
+            s_root[1] = heap ? gr[1] : KO::empty();
         }
         __syncthreads();
+    } else {
+    // ---- initial state
+        for (int i = tid; i < L.W; i += kLoopThreads) { st.ins[i] = 0; st.vmark[i] = 0; st.rnd[i] = 0; }
+        for (int w = tid; w < n; w += kLoopThreads) {
+            st.ptr[w] = 0;
+            const uint16_t m0 = a.idx[(long long)w * a.ldi];
+            st.mc[w] = m0 < n ? m0 : kNone16;
+        }
+        for (int f = tid; f < L.nfmax; f += kLoopThreads) {
+            st.fv[f] = kNone16;
+            st.tf.leaf[f] = KO::empty();
+            if (heap) {
+                st.ts.leaf[f] = KO::empty();
+                st.pend_key[f] = KO::empty();
+            }
+        }
+        auto clear_tree = [&](Tree<KO> &x) {
+            for (int g = tid; g < L.G1; g += kLoopThreads) x.l1[g] = KO::empty();
+            for (int g = tid; g < L.G2; g += kLoopThreads) x.l2[g] = KO::empty();
+            for (int i = tid; i < (L.G1 + 31) / 32; i += kLoopThreads) x.b1[i] = 0;
+            for (int i = tid; i < (L.G2 + 31) / 32; i += kLoopThreads) x.b2[i] = 0;
+        };
+        clear_tree(st.tf);
+        if (heap) clear_tree(st.ts);
+        if (tid == 0) {
+            s_nf = 4; s_k = 0; s_vcount = 0; s_scan = 0; s_evals = 0; s_stop = 0; s_nsel = 0;
+            s_fcount = 0;
+            s_n1[0] = s_n1[1] = s_n2[0] = s_n2[1] = 0;
+            s_root[0] = s_root[1] = KO::empty();
+        }
+        __syncthreads();
+
+        // ---- initial 4-clique: top four row sums (r desc, id asc)
+        for (int c = 0; c < 4; ++c) {
+            long long br = LLONG_MIN;
+            int bi = INT_MAX;
+            for (int v = tid; v < n; v += kLoopThreads) {
+                bool taken = false;
+                for (int j = 0; j < c; ++j) taken |= (s_clique[j] == v);
+                if (taken) continue;
+                const long long r = a.rowsum[v];
+                if (r > br || (r == br && v < bi)) { br = r; bi = v; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long r2 = __shfl_xor_sync(0xffffffffu, br, o);
+                const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (r2 > br || (r2 == br && i2 < bi)) { br = r2; bi = i2; }
+            }
+            if (lane == 0) { s_red_r[warp] = br; s_red_i[warp] = bi; }
+            __syncthreads();
+            if (tid == 0) {
+                long long r = s_red_r[0];
+                int i = s_red_i[0];
+                for (int w = 1; w < kLoopWarps; ++w)
+                    if (s_red_r[w] > r || (s_red_r[w] == r && s_red_i[w] < i)) { r = s_red_r[w]; i = s_red_i[w]; }
+                s_clique[c] = i;
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            const int *c = s_clique;
+            for (int i = 0; i < 4; ++i) {
+                a.order[i] = c[i];
+                st.ins[c[i] >> 5] |= 1u << (c[i] & 31);
+            }
+            const int pr[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+            for (int i = 0; i < 6; ++i) {
+                a.edges[2 * i] = c[pr[i][0]];
+                a.edges[2 * i + 1] = c[pr[i][1]];
+            }
+            a.parent[0] = -1;
+            const int tri[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
+            for (int f = 0; f < 4; ++f) {
+                int p = c[tri[f][0]], q = c[tri[f][1]], r = c[tri[f][2]], t;
+                if (p > q) { t = p; p = q; q = t; }
+                if (q > r) { t = q; q = r; r = t; }
+                if (p > q) { t = p; p = q; q = t; }
+                a.face[f] = make_int4(p, q, r, 0);
+                a.fu_buf[f] = f | (kToFresh << 28);
+            }
+        }
+        __syncthreads();
+        st.recompute(a.fu_buf, 4);
+        st.update(heap);
     }
-    if (tid == 0) {
-        const int *c = s_clique;
-        for (int i = 0; i < 4; ++i) {
-            a.order[i] = c[i];
-            st.ins[c[i] >> 5] |= 1u << (c[i] & 31);
-        }
-        const int pr[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
-        for (int i = 0; i < 6; ++i) {
-            a.edges[2 * i] = c[pr[i][0]];
-            a.edges[2 * i + 1] = c[pr[i][1]];
-        }
-        a.parent[0] = -1;
-        const int tri[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
-        for (int f = 0; f < 4; ++f) {
-            int p = c[tri[f][0]], q = c[tri[f][1]], r = c[tri[f][2]], t;
-            if (p > q) { t = p; p = q; q = t; }
-            if (q > r) { t = q; q = r; r = t; }
-            if (p > q) { t = p; p = q; q = t; }
-            a.face[f] = make_int4(p, q, r, 0);
-            st.flist[f] = f;
-        }
-    }
-    __syncthreads();
-    st.recompute(st.flist, 4);
-    st.tree_update();
 
     // ---- main loop
     const int total = n - 4;
+    const int k_stop = a.k_stop < total ? a.k_stop : total;
     long long stale = 0, rounds = 0;
-    while (s_k < total) {
+    long long cyc_rec = 0, cyc_tree = 0, cyc_sel = 0;
+    long long cyc_x = 0, cyc_v = 0, cyc_sim = 0, cyc_scan = 0, n_epoch_iters = 0, n_x = 0;
+    long long c_mark = clock64();
+    auto lap = [&](long long &acc) {
+        const long long c = clock64();
+        acc += c - c_mark;
+        c_mark = c;
+    };
+    while (s_k < k_stop) {
         if (tid == 0 && globaltimer_ns() - t0 > a.timeout_ns) s_stop = TMFG_ETIMEOUT;
         __syncthreads();
         if (s_stop) break;
-        if (a.mode == TMFG_HEAP) {
-            const Node r = s_root;
-            if (r.gk == 0ull || r.v >= n || r.f >= s_nf) {
+        if (heap) {
+            // ---- resolve the epoch: which pair does Algorithm 2 insert next?
+            // Stale faces are taken in key order, at most 8 level-1 groups
+            // (256 faces) at a time: the stale keys >= tau, tau = the 8th
+            // largest group maximum (or the best fresh key if fewer than 8
+            // groups rank above it).  Every stale key above tau is in the
+            // batch, so the batch is a prefix of the key order.
+            for (;;) {
+                const Key kf = s_root[0], ks = s_root[1];
+                if (!KO::gt(ks, kf)) {
+                    if (tid == 0) s_win = kf;
+                    __syncthreads();
+                    break;
+                }
+                long long e0 = clock64();
+                ++n_epoch_iters;
+                if (tid == 0) { s_nx = 0; s_ninv = 0; s_tau = kf; s_nq1 = 0; }
+                // (a) the top 8 level-2 groups above kf
+                if (tid < 64) {
+                    const Key x = tid < L.G2 ? st.ts.l2[tid] : KO::empty();
+                    st.xkey[tid] = x;
+                }
+                __syncthreads();
+                if (tid < 64) {
+                    const Key x = st.xkey[tid];
+                    if (KO::gt(x, kf)) {
+                        int r = 0;
+                        for (int j = 0; j < 64; ++j) r += KO::gt(st.xkey[j], x);
+                        if (r < 8) st.q2x[r] = (uint16_t)tid;
+                    }
+                }
+                __syncthreads();
+                int nq2 = 0;
+                for (int j = 0; j < 64 && j < L.G2; ++j) nq2 += KO::gt(st.xkey[j], kf);
+                nq2 = nq2 < 8 ? nq2 : 8;
+                __syncthreads();
+                // (b) their level-1 nodes; the top 8 above kf give tau
+                {
+                    const int gi = tid >> 5, j = gi < nq2 ? st.q2x[gi] * 32 + (tid & 31) : -1;
+                    const Key x = (j >= 0 && j < L.G1) ? st.ts.l1[j] : KO::empty();
+                    st.xpend[tid] = KO::gt(x, kf) ? x : KO::empty();
+                    __syncthreads();
+                    const Key y = st.xpend[tid];
+                    if (!KO::is_empty(y)) {
+                        int r = 0;
+                        for (int q = 0; q < kLoopThreads; ++q) r += KO::gt(st.xpend[q], y);
+                        if (r < 8) st.q1x[r] = (uint16_t)j;
+                        if (r == 7) s_tau = y;
+                        atomicAdd(&s_nq1, 1);
+                    }
+                }
+                __syncthreads();
+                const int nq1 = s_nq1 < 8 ? s_nq1 : 8;
+                const Key tau = s_tau;  // kf when fewer than 8 groups qualify
+                // (c) the leaves >= tau (and > kf) of those groups
+                {
+                    const int gi = tid >> 5;
+                    if (gi < nq1) {
+                        const int f = st.q1x[gi] * 32 + (tid & 31);
+                        if (f < L.nfmax) {
+                            const Key kk = st.ts.leaf[f];
+                            if (KO::gt(kk, kf) && !KO::gt(tau, kk)) {
+                                const int pos = atomicAdd(&s_nx, 1);
+                                st.xf[pos] = f;
+                                st.xkey[pos] = kk;
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+                long long e1 = clock64();
+                cyc_x += e1 - e0;
+                const int nx = s_nx;
+                n_x += nx;
+                // pending results still valid? (recompute the others)
+                for (int i = tid; i < nx; i += kLoopThreads) {
+                    const int f = st.xf[i];
+                    if (!st.pend_valid(f)) a.fu_buf[atomicAdd(&s_ninv, 1)] = f | (kToPend << 28);
+                }
+                __syncthreads();
+                if (s_ninv) st.recompute(a.fu_buf, s_ninv);
+                long long e2 = clock64();
+                cyc_v += e2 - e1;
+                for (int i = tid; i < nx; i += kLoopThreads) {
+                    st.xpend[i] = st.pend_key[st.xf[i]];
+                    int r = 0;
+                    const Key ki = st.xkey[i];
+                    for (int j = 0; j < nx; ++j) r += KO::gt(st.xkey[j], ki);
+                    st.xs[r] = (uint16_t)i;
+                }
+                __syncthreads();
+                // the pops of Algorithm 2, in key order
+                if (tid == 0) {
+                    Key run = kf;
+                    int np = 0;
+                    for (int r = 0; r < nx; ++r) {
+                        const int i = st.xs[r];
+                        if (!KO::gt(st.xkey[i], run)) break;
+                        ++np;
+                        if (KO::gt(st.xpend[i], run)) run = st.xpend[i];
+                    }
+                    s_np = np;
+                    s_win = run;
+                    // the whole batch was popped and more stale keys may rank
+                    // above the running best: resolve the next batch
+                    s_more = (np == nx && KO::gt(tau, kf)) ? 1 : 0;
+                }
+                __syncthreads();
+                const int np = s_np;
+                for (int r = tid; r < np; r += kLoopThreads) {
+                    const int i = st.xs[r];
+                    const int f = st.xf[i];
+                    const Key p = st.xpend[i];
+                    st.tf.set(f, p);
+                    st.fv[f] = KO::is_empty(p) ? kNone16 : (uint16_t)KO::vert(p);
+                    st.ts.set(f, KO::empty());
+                }
+                stale += np;
+                cyc_sim += clock64() - e2;
+                st.update(1);
+                if (!s_more) break;
+                if (tid == 0 && globaltimer_ns() - t0 > a.timeout_ns) s_stop = TMFG_ETIMEOUT;
+                __syncthreads();
+                if (s_stop) break;
+            }
+            if (s_stop) break;
+            lap(cyc_sel);
+            const Key w = s_win;
+            const int v = KO::vert(w), fs = KO::face(w);
+            if (KO::is_empty(w) || v >= n || fs >= s_nf || st.is_ins(v)) {
                 if (tid == 0) s_stop = TMFG_EINTERNAL;
                 __syncthreads();
                 break;
             }
-            if (st.is_ins(r.v)) {
-                // stale pair: recompute this face alone and re-push it
-                ++stale;
-                if (tid == 0) st.flist[0] = r.f;
-                __syncthreads();
-                st.recompute(st.flist, 1);
-                st.tree_update();
-                continue;
+            // ---- insert, then recompute the new faces and the faces it made stale
+            const int nf_old = s_nf;
+            if (tid == 0) {
+                st.insert_pair(v, fs);
+                a.fu_buf[0] = fs | (kToFresh << 28);
+                a.fu_buf[1] = nf_old | (kToFresh << 28);
+                a.fu_buf[2] = (nf_old + 1) | (kToFresh << 28);
+                s_fcount = 3;
             }
-            if (tid == 0) st.insert_pair(r.v, r.f, st.flist);
             __syncthreads();
+            {
+                const uint32_t vv = (uint32_t)v | ((uint32_t)v << 16);
+                const uint4 *fv8 = reinterpret_cast<const uint4 *>(st.fv);
+                for (int i = tid; 8 * i < nf_old; i += kLoopThreads) {
+                    const uint4 q = fv8[i];
+                    const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const uint32_t m = __vcmpeq2(wd[h], vv);
+                        if (m) {
+#pragma unroll
+                            for (int b = 0; b < 2; ++b) {
+                                const int f = 8 * i + 2 * h + b;
+                                if (f < nf_old && f != fs && ((m >> (16 * b)) & 0xFFFFu))
+                                    a.fu_buf[atomicAdd(&s_fcount, 1)] = f | (kToPendMove << 28);
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            {
+                long long c = clock64();
+                cyc_scan += c - c_mark;
+            }
             ++rounds;
-            st.recompute(st.flist, 3);
-            st.tree_update();
+            st.recompute(a.fu_buf, s_fcount);
+            lap(cyc_rec);
+            st.update(1);
+            lap(cyc_tree);
         } else {
-            // L = the P best pairs (repeated extraction from the max index)
+            // L = the P best pairs (repeated extraction from the index)
             if (tid == 0) s_nsel = 0;
             __syncthreads();
             for (int i = 0; i < a.P; ++i) {
-                const Node r = s_root;
-                if (r.gk == 0ull) break;
+                const Key r = s_root[0];
+                if (KO::is_empty(r)) break;
                 if (tid == 0) {
                     st.sel[s_nsel++] = r;
-                    if (a.P > 1) {
-                        a.leaf_gk[r.f] = 0ull;
-                        a.leaf_v[r.f] = INT_MAX;
-                        st.mark_d1(r.f >> 5);
-                    }
+                    if (a.P > 1) st.tf.set(KO::face(r), KO::empty());
                 }
                 __syncthreads();
                 if (a.P == 1) break;
-                st.tree_update();
+                st.update(0);
             }
             const int nsel = s_nsel;
             if (nsel == 0) {
@@ -517,12 +952,12 @@ __global__ void __launch_bounds__(kLoopThreads, 1) tmfg_loop_kernel(LoopArgs a)
                 __syncthreads();
                 break;
             }
+            lap(cyc_sel);
             const int nf_old = s_nf;
             if (tid == 0) {
                 // keep the first (best) pair of each vertex, insert in rank order
-                int out3[3];
                 for (int i = 0; i < nsel; ++i) {
-                    const int v = st.sel[i].v;
+                    const int v = KO::vert(st.sel[i]);
                     if (v >= n) {
                         s_stop = TMFG_EINTERNAL;
                         continue;
@@ -534,7 +969,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) tmfg_loop_kernel(LoopArgs a)
                         continue;
                     }
                     st.rnd[v >> 5] |= 1u << (v & 31);
-                    st.insert_pair(v, st.sel[i].f, out3);
+                    st.insert_pair(v, KO::face(st.sel[i]));
                 }
                 s_fcount = 0;
             }
@@ -544,51 +979,198 @@ __global__ void __launch_bounds__(kLoopThreads, 1) tmfg_loop_kernel(LoopArgs a)
             // F_update: faces whose stored vertex was inserted this round,
             // and the appended faces
             const int nf_new = s_nf;
-            for (int f = tid; f < nf_old; f += kLoopThreads) {
-                const int v = st.fv[f];
-                if (v != kNone16 && ((st.rnd[v >> 5] >> (v & 31)) & 1u))
-                    a.fu_buf[atomicAdd(&s_fcount, 1)] = f;
+            if (nsel == 1) {
+                // one inserted vertex: compare 8 stored vertices per 16-byte load
+                const int v = KO::vert(st.sel[0]);
+                const uint32_t vv = (uint32_t)v | ((uint32_t)v << 16);
+                const uint4 *fv8 = reinterpret_cast<const uint4 *>(st.fv);
+                for (int i = tid; 8 * i < nf_old; i += kLoopThreads) {
+                    const uint4 q = fv8[i];
+                    const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const uint32_t m = __vcmpeq2(wd[h], vv);
+                        if (m) {
+#pragma unroll
+                            for (int b = 0; b < 2; ++b) {
+                                const int f = 8 * i + 2 * h + b;
+                                if (f < nf_old && ((m >> (16 * b)) & 0xFFFFu))
+                                    a.fu_buf[atomicAdd(&s_fcount, 1)] = f | (kToFresh << 28);
+                            }
+                        }
+                    }
+                }
+            } else {
+                for (int f = tid; f < nf_old; f += kLoopThreads) {
+                    const int v = st.fv[f];
+                    if (v != kNone16 && ((st.rnd[v >> 5] >> (v & 31)) & 1u))
+                        a.fu_buf[atomicAdd(&s_fcount, 1)] = f | (kToFresh << 28);
+                }
             }
             for (int f = nf_old + tid; f < nf_new; f += kLoopThreads)
-                a.fu_buf[atomicAdd(&s_fcount, 1)] = f;
+                a.fu_buf[atomicAdd(&s_fcount, 1)] = f | (kToFresh << 28);
             __syncthreads();
             st.recompute(a.fu_buf, s_fcount);
+            lap(cyc_rec);
             if (tid == 0)
                 for (int i = 0; i < nsel; ++i) {
-                    const int v = st.sel[i].v;
+                    const int v = KO::vert(st.sel[i]);
                     if (v < n) st.rnd[v >> 5] &= ~(1u << (v & 31));
                 }
-            st.tree_update();
+            st.update(0);
+            lap(cyc_tree);
         }
     }
+    // ---- statistics (summed over segments) and the state for the next segment
+    __syncthreads();
     if (tid == 0) {
         if (s_stop) set_status(a.status, s_stop);
-        a.stats[0] = s_evals;
-        a.stats[1] = stale;
-        a.stats[2] = s_scan;
-        a.stats[3] = rounds;
-        a.stats[4] = (long long)(globaltimer_ns() - t0);
+        const long long seg[16] = {s_evals, stale, s_scan, rounds,
+                                   (long long)(globaltimer_ns() - t0), cyc_rec, cyc_tree, cyc_sel,
+                                   st.cyc_push, st.cyc_refresh, st.cyc_gain, cyc_x, cyc_v,
+                                   cyc_sim, cyc_scan, n_epoch_iters};
+        for (int i = 0; i < 16; ++i) {
+            acc[i] += seg[i];
+            a.stats[i] = acc[i];
+            gscal[i] = acc[i];
+        }
+        gscal[16] = s_nf;
+        gscal[17] = s_k;
+        Key *gr = reinterpret_cast<Key *>(gs + SL.off_roots);
+        gr[0] = s_root[0];
+        gr[1] = s_root[1];
+    }
+    if (s_k < total && !s_stop) {
+        uint32_t *gins = reinterpret_cast<uint32_t *>(gs + SL.off_ins);
+        uint16_t *gmc = reinterpret_cast<uint16_t *>(gs + SL.off_mc);
+        uint16_t *gptr = reinterpret_cast<uint16_t *>(gs + SL.off_ptr);
+        uint16_t *gfv = reinterpret_cast<uint16_t *>(gs + SL.off_fv);
+        for (int i = tid; i < L.W; i += kLoopThreads) gins[i] = st.ins[i];
+        for (int w = tid; w < n; w += kLoopThreads) { gmc[w] = st.mc[w]; gptr[w] = st.ptr[w]; }
+        for (int f = tid; f < L.nfmax; f += kLoopThreads) gfv[f] = st.fv[f];
+        auto save_tree = [&](Tree<KO> &x, int t) {
+            Key *g = reinterpret_cast<Key *>(gs + SL.off_tree[t]);
+            for (int i = tid; i < L.G1; i += kLoopThreads) g[i] = x.l1[i];
+            for (int i = tid; i < L.G2; i += kLoopThreads) g[L.G1 + i] = x.l2[i];
+        };
+        save_tree(st.tf, 0);
+        if (heap) save_tree(st.ts, 1);
     }
 }
 
-size_t loop_smem_bytes(int n) { return loop_layout(n).total; }
+// Between loop segments: drop the inserted ids from every sorted row.  Row
+// w keeps, in order, the ids after ptr[w] that are still uninserted, moved to
+// the front of the row and ended by 0xFFFF; ptr[w] = 0 and Mc[w] = the new
+// first id.  MaxCorrs (the first uninserted id of the sorted row) is
+// unchanged by construction.  One CTA per row, grid-stride; reads stay
+// ahead of writes within a row, so the compaction is in place.
+__global__ void __launch_bounds__(256) compact_rows_kernel(uint16_t *idx, long long ldi, int n,
+                                                           void *state, const int *status)
+{
+    __shared__ int s_cnt[8], s_end;
+    if (*(volatile const int *)status != 0) return;
+    const StateLayout SL = state_layout(n, sizeof(Key128));
+    unsigned char *gs = reinterpret_cast<unsigned char *>(state);
+    const uint32_t *ins = reinterpret_cast<const uint32_t *>(gs + SL.off_ins);
+    uint16_t *gmc = reinterpret_cast<uint16_t *>(gs + SL.off_mc);
+    uint16_t *gptr = reinterpret_cast<uint16_t *>(gs + SL.off_ptr);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int mlen = n - 1;
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        uint16_t *row = idx + (long long)w * ldi;
+        const int p0 = gptr[w];
+        int out = 0;
+        if (tid == 0) s_end = 0;
+        __syncthreads();
+        for (int base = p0; base < mlen; base += 256) {
+            const int q = base + tid;
+            const int e = q < mlen ? row[q] : kNone16;
+            const bool end = e >= n;  // 0xFFFF ends the row
+            const bool keep = !end && !((ins[e >> 5] >> (e & 31)) & 1u);
+            const unsigned endb = __ballot_sync(0xffffffffu, end);
+            if (lane == 0 && endb) atomicOr(&s_end, 1);
+            // keep entries before the first end marker only
+            __syncthreads();
+            const int any_end = s_end;
+            int endpos = 0x7FFFFFFF;
+            if (any_end) {
+                // first end marker in this chunk (block-wide min)
+                const int mine = end ? q : 0x7FFFFFFF;
+                int m = mine;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if (lane == 0) s_cnt[warp] = m;
+                __syncthreads();
+                for (int i = 0; i < 8; ++i) endpos = min(endpos, s_cnt[i]);
+                __syncthreads();
+            }
+            const bool k2 = keep && q < endpos;
+            const unsigned kb = __ballot_sync(0xffffffffu, k2);
+            if (lane == 0) s_cnt[warp] = __popc(kb);
+            __syncthreads();
+            int before = 0, tot = 0;
+            for (int i = 0; i < 8; ++i) {
+                before += i < warp ? s_cnt[i] : 0;
+                tot += s_cnt[i];
+            }
+            __syncthreads();
+            if (k2) row[out + before + __popc(kb & ((1u << lane) - 1u))] = (uint16_t)e;
+            out += tot;
+            __syncthreads();
+            if (any_end) break;
+        }
+        if (tid == 0) {
+            if (out < ldi) row[out] = kNone16;
+            gptr[w] = 0;
+            gmc[w] = out > 0 ? row[0] : kNone16;
+        }
+        __syncthreads();
+    }
+}
 
+size_t loop_smem_bytes(int n, int dtype, int mode)
+{
+    const size_t ks = dtype == TMFG_F32 ? sizeof(unsigned long long) : sizeof(Key128);
+    return loop_layout(n, ks, mode == TMFG_HEAP ? 2 : 1).total;
+}
+
+// The insertion loop runs in segments; between them every sorted row is
+// compacted to its uninserted ids, so the lazy pointers keep finding an
+// uninserted id in their first probe.  Segments end after 1/2, 3/4, 7/8,
+// 15/16, 31/32 of the insertions (for n >= 1024).
 int launch_loop(const LoopArgs &args, int dtype, cudaStream_t stream)
 {
-    const size_t smem = loop_smem_bytes(args.n);
-    if (smem > 232448) return TMFG_ETOOBIG;
-    if (dtype == TMFG_F32) {
-        auto k = tmfg_loop_kernel<float>;
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return TMFG_ECUDA;
-        k<<<1, kLoopThreads, smem, stream>>>(args);
-    } else {
-        auto k = tmfg_loop_kernel<double>;
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return TMFG_ECUDA;
-        k<<<1, kLoopThreads, smem, stream>>>(args);
+    const size_t smem = loop_smem_bytes(args.n, dtype, args.mode);
+    if (smem > kSmemLimit || 2 * (size_t)args.n - 4 > 65535) return TMFG_ETOOBIG;
+    auto kf = tmfg_loop_kernel<float>;
+    auto kd = tmfg_loop_kernel<double>;
+    if (cudaFuncSetAttribute(dtype == TMFG_F32 ? (const void *)kf : (const void *)kd,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return TMFG_ECUDA;
+    const int total = args.n - 4;
+    int stops[8];
+    int ns = 0;
+    if (args.n >= 1024)
+        for (int j = 1; j <= 5; ++j) {
+            const int s = total - (total >> j);
+            if (s > 0 && (ns == 0 || s > stops[ns - 1])) stops[ns++] = s;
+        }
+    stops[ns++] = total;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int i = 0; i < ns; ++i) {
+        LoopArgs a = args;
+        a.k_stop = stops[i];
+        a.resume = i > 0;
+        if (dtype == TMFG_F32)
+            kf<<<1, kLoopThreads, smem, stream>>>(a);
+        else
+            kd<<<1, kLoopThreads, smem, stream>>>(a);
+        if (i + 1 < ns)
+            compact_rows_kernel<<<2 * sms, 256, 0, stream>>>(const_cast<uint16_t *>(args.idx),
+                                                             args.ldi, args.n, args.state,
+                                                             args.status);
     }
     return cudaGetLastError() == cudaSuccess ? TMFG_OK : TMFG_ECUDA;
 }

@@ -247,7 +247,7 @@ def run_ours(args, rank, world, local):
 
         def e2e_step():
             Sd.copy_(Sh, non_blocking=True)
-            T.tmfg_build(ctx, Sd, "heap", 1, out=out, stream=stream)
+            T.tmfg_build(ctx, Sd, MODE, 1, out=out, stream=stream)
             T.tmfg_apsp(ctx, Sd, out["edges"], D=D, stream=stream)
             T.tmfg_apsp(ctx, Sd, out["edges"], approx=True, D=Da, stream=stream)
             Eh.copy_(out["edges"], non_blocking=True)

@@ -440,22 +440,32 @@ struct Loop {
         }
     }
 
-    // Level-1 recompute of the marked groups of index x (warp per group).
+    // Level-1 recompute of the marked groups of index x: a warp takes up to 4
+    // groups at once, with all their leaf loads in flight together.
     __device__ void update_l1(Tree<KO> &x)
     {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         const int c1 = *x.n1;
-        for (int i = warp; i < c1; i += kLoopWarps) {
-            const int g = x.q1[i];
-            const int f = g * 32 + lane;
-            Key v = f < nfmax ? x.leaf[f] : KO::empty();
-            v = warp_max<KO>(v);
-            if (lane == 0) {
-                x.l1[g] = v;
-                atomicAnd(&x.b1[g >> 5], ~(1u << (g & 31)));
-                const int g2 = g >> 5;
-                const uint32_t bit = 1u << (g2 & 31);
-                if (!(atomicOr(&x.b2[g2 >> 5], bit) & bit)) x.q2[atomicAdd(x.n2, 1)] = (uint16_t)g2;
+        for (int i0 = 4 * warp; i0 < c1; i0 += 4 * kLoopWarps) {
+            Key v[4];
+            int g[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                g[u] = i0 + u < c1 ? x.q1[i0 + u] : -1;
+                const int f = g[u] * 32 + lane;
+                v[u] = (g[u] >= 0 && f < nfmax) ? x.leaf[f] : KO::empty();
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (g[u] < 0) break;
+                const Key m = warp_max<KO>(v[u]);
+                if (lane == 0) {
+                    x.l1[g[u]] = m;
+                    atomicAnd(&x.b1[g[u] >> 5], ~(1u << (g[u] & 31)));
+                    const int g2 = g[u] >> 5;
+                    const uint32_t bit = 1u << (g2 & 31);
+                    if (!(atomicOr(&x.b2[g2 >> 5], bit) & bit)) x.q2[atomicAdd(x.n2, 1)] = (uint16_t)g2;
+                }
             }
         }
     }
@@ -1062,8 +1072,10 @@ __global__ void __launch_bounds__(kLoopThreads, 1) tmfg_loop_kernel(LoopArgs a)
 // w keeps, in order, the ids after ptr[w] that are still uninserted, moved to
 // the front of the row and ended by 0xFFFF; ptr[w] = 0 and Mc[w] = the new
 // first id.  MaxCorrs (the first uninserted id of the sorted row) is
-// unchanged by construction.  One CTA per row, grid-stride; reads stay
-// ahead of writes within a row, so the compaction is in place.
+// unchanged by construction.  One CTA per row (grid-stride); each thread
+// reads 8 ids with one 16-byte load, so a round covers 2048 ids; a round's
+// reads all happen before its writes, and writes land at or before the read
+// positions, so the compaction is in place.
 __global__ void __launch_bounds__(256) compact_rows_kernel(uint16_t *idx, long long ldi, int n,
                                                            void *state, const int *status)
 {
@@ -1080,44 +1092,64 @@ __global__ void __launch_bounds__(256) compact_rows_kernel(uint16_t *idx, long l
         uint16_t *row = idx + (long long)w * ldi;
         const int p0 = gptr[w];
         int out = 0;
-        if (tid == 0) s_end = 0;
-        __syncthreads();
-        for (int base = p0; base < mlen; base += 256) {
-            const int q = base + tid;
-            const int e = q < mlen ? row[q] : kNone16;
-            const bool end = e >= n;  // 0xFFFF ends the row
-            const bool keep = !end && !((ins[e >> 5] >> (e & 31)) & 1u);
-            const unsigned endb = __ballot_sync(0xffffffffu, end);
-            if (lane == 0 && endb) atomicOr(&s_end, 1);
-            // keep entries before the first end marker only
-            __syncthreads();
-            const int any_end = s_end;
-            int endpos = 0x7FFFFFFF;
-            if (any_end) {
-                // first end marker in this chunk (block-wide min)
-                const int mine = end ? q : 0x7FFFFFFF;
-                int m = mine;
+        bool done = false;
+        for (int base = p0 & ~7; base < mlen && !done; base += 2048) {
+            const int q0 = base + 8 * tid;
+            uint16_t e[8];
+            if (q0 < ldi) {
+                const uint4 c = *reinterpret_cast<const uint4 *>(row + q0);
+                e[0] = c.x & 0xFFFF; e[1] = c.x >> 16; e[2] = c.y & 0xFFFF; e[3] = c.y >> 16;
+                e[4] = c.z & 0xFFFF; e[5] = c.z >> 16; e[6] = c.w & 0xFFFF; e[7] = c.w >> 16;
+            } else {
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
-                if (lane == 0) s_cnt[warp] = m;
-                __syncthreads();
-                for (int i = 0; i < 8; ++i) endpos = min(endpos, s_cnt[i]);
-                __syncthreads();
+                for (int t = 0; t < 8; ++t) e[t] = kNone16;
             }
-            const bool k2 = keep && q < endpos;
-            const unsigned kb = __ballot_sync(0xffffffffu, k2);
-            if (lane == 0) s_cnt[warp] = __popc(kb);
+            // phase 1: the first end marker of the round (an id >= n or the
+            // row end), block-wide
+            int first_end = 8;
+#pragma unroll
+            for (int t = 7; t >= 0; --t) {
+                const int q = q0 + t;
+                if (q >= mlen || e[t] >= n) first_end = t;
+            }
+            int m = first_end < 8 ? q0 + first_end : 0x7FFFFFFF;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (tid == 0) s_end = 0x7FFFFFFF;
+            __syncthreads();
+            if (lane == 0) atomicMin(&s_end, m);
+            __syncthreads();
+            const int gend = s_end;
+            // phase 2: keep the uninserted ids in [p0, gend), compact in order
+            uint32_t keepm = 0;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int q = q0 + t;
+                if (q >= p0 && q < gend && !((ins[e[t] >> 5] >> (e[t] & 31)) & 1u))
+                    keepm |= 1u << t;
+            }
+            const int c = __popc(keepm);
+            int x = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) s_cnt[warp] = x;
             __syncthreads();
             int before = 0, tot = 0;
+#pragma unroll
             for (int i = 0; i < 8; ++i) {
                 before += i < warp ? s_cnt[i] : 0;
                 tot += s_cnt[i];
             }
-            __syncthreads();
-            if (k2) row[out + before + __popc(kb & ((1u << lane) - 1u))] = (uint16_t)e;
+            int pos = out + before + x - c;
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                if ((keepm >> t) & 1u) row[pos++] = e[t];
             out += tot;
+            done = gend != 0x7FFFFFFF;
             __syncthreads();
-            if (any_end) break;
         }
         if (tid == 0) {
             if (out < ldi) row[out] = kNone16;

@@ -131,6 +131,37 @@ int tmfg_apsp(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, int32_t dtype
               const int32_t *edges, const tmfg_apsp_params *params, float *D, int64_t ldd,
               void *stream);
 
+/* One instance of a batched run (all pointers device, caller-owned). */
+typedef struct {
+    const void *S;          /* n x n similarity matrix, leading dimension ld */
+    int64_t n, ld;
+    int32_t *order;         /* [n]        as for tmfg_build */
+    int32_t *edges;         /* [(3n-6)*2] */
+    int32_t *ins_face;      /* [(n-4)*3]  (may be NULL when n == 4) */
+    int32_t *bubble_parent; /* [n-3] */
+    float *D;               /* exact APSP output (n x n, ldd), or NULL to skip */
+    int64_t ldd;
+} tmfg_job;
+
+/* Launch shapes of a batched run; 0 fields take the defaults.  Chosen by an
+ * autotuner on the Python side (paper_2408_09399_gb300.autotune). */
+typedef struct {
+    int32_t sssp_threads;   /* threads per search CTA: 256 or 512 (default) */
+} tmfg_batch_config;
+
+/* Many TMFG constructions (and optionally exact APSPs) in one launch per
+ * stage: one persistent grid sorts the rows of every matrix, one CTA per
+ * instance runs its insertion loop, and one persistent grid runs every
+ * (instance, source) search.  Every instance gets exactly the result
+ * tmfg_build (and tmfg_apsp) gives it alone.  `jobs` is a HOST array of
+ * `count` descriptors; all instances share `params` (same dtype and mode);
+ * each n must satisfy 4 <= n <= tmfg_max_n(dtype).  Asynchronous; the
+ * descriptors are copied through the context's pinned staging buffer, so
+ * the host array may be reused once the call returns.  The loop runs in one
+ * segment per instance (no row compaction), which suits small instances. */
+int tmfg_batch_run(tmfg_ctx *ctx, const tmfg_job *jobs, int32_t count, const tmfg_params *params,
+                   const tmfg_batch_config *cfg, void *stream);
+
 /* Largest n accepted by tmfg_apsp_exact_noalloc. */
 #define TMFG_NOALLOC_MAX_N 21581
 

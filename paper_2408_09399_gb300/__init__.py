@@ -39,6 +39,17 @@ class _Params(ctypes.Structure):
                 ("flags", ctypes.c_uint32)]
 
 
+class _Job(ctypes.Structure):
+    _fields_ = [("S", ctypes.c_void_p), ("n", ctypes.c_int64), ("ld", ctypes.c_int64),
+                ("order", ctypes.c_void_p), ("edges", ctypes.c_void_p),
+                ("ins_face", ctypes.c_void_p), ("bubble_parent", ctypes.c_void_p),
+                ("D", ctypes.c_void_p), ("ldd", ctypes.c_int64)]
+
+
+class _BatchConfig(ctypes.Structure):
+    _fields_ = [("sssp_threads", ctypes.c_int32)]
+
+
 class _ApspParams(ctypes.Structure):
     _fields_ = [("approx", ctypes.c_int32), ("n_hubs", ctypes.c_int32),
                 ("radius_factor", ctypes.c_float)]
@@ -69,6 +80,9 @@ def load_library():
         lib.tmfg_row_sort.restype = ctypes.c_int
         lib.tmfg_apsp.argtypes = [P, P, i64, i64, i32, P, ctypes.POINTER(_ApspParams), P, i64, P]
         lib.tmfg_apsp.restype = ctypes.c_int
+        lib.tmfg_batch_run.argtypes = [P, ctypes.POINTER(_Job), ctypes.c_int32,
+                                       ctypes.POINTER(_Params), ctypes.POINTER(_BatchConfig), P]
+        lib.tmfg_batch_run.restype = ctypes.c_int
         lib.tmfg_sync_status.argtypes = [P, P]
         lib.tmfg_sync_status.restype = ctypes.c_int
         lib.tmfg_last_stats.argtypes = [P, P, ctypes.c_int]
@@ -225,6 +239,43 @@ def tmfg_apsp(ctx: Context, S, edges, approx: bool = False, n_hubs: int = 0,
                                   _dev_ptr(D, torch.float32), D.stride(0), _stream_handle(stream))
     _check(rc, "tmfg_apsp")
     return D
+
+
+def tmfg_batch_run(ctx: Context, mats, mode: str = "corr", prefix: int = 1, apsp: bool = True,
+                   sssp_threads: int = 0, outs=None, stream=None):
+    """TMFG (and exact APSP when ``apsp``) of every matrix in ``mats`` (CUDA
+    tensors of one dtype) with one launch per stage.  Returns a list of dicts
+    like tmfg_build's, plus "D" when ``apsp``.  Asynchronous."""
+    torch = _torch()
+    if not mats:
+        return []
+    dt = _mat_dtype(mats[0])
+    if outs is None:
+        outs = []
+        for S in mats:
+            n = S.shape[0]
+            o = {"order": torch.empty(n, dtype=torch.int32, device=S.device),
+                 "edges": torch.empty((3 * n - 6, 2), dtype=torch.int32, device=S.device),
+                 "ins_face": torch.empty((max(n - 4, 1), 3), dtype=torch.int32, device=S.device),
+                 "bubble_parent": torch.empty(n - 3, dtype=torch.int32, device=S.device)}
+            if apsp:
+                o["D"] = torch.empty((n, n), dtype=torch.float32, device=S.device)
+            outs.append(o)
+    jobs = (_Job * len(mats))()
+    for i, (S, o) in enumerate(zip(mats, outs)):
+        if _mat_dtype(S) != dt:
+            raise TypeError("all matrices of a batch must have the same dtype")
+        n = S.shape[0]
+        D = o.get("D") if apsp else None
+        jobs[i] = _Job(S.data_ptr(), n, S.stride(0), o["order"].data_ptr(), o["edges"].data_ptr(),
+                       o["ins_face"].data_ptr(), o["bubble_parent"].data_ptr(),
+                       D.data_ptr() if D is not None else None, D.stride(0) if D is not None else 0)
+    p = _Params({"corr": TMFG_CORR, "heap": TMFG_HEAP}[mode], int(prefix), dt, 0)
+    cfg = _BatchConfig(int(sssp_threads))
+    rc = load_library().tmfg_batch_run(ctx.handle, jobs, len(mats), ctypes.byref(p),
+                                       ctypes.byref(cfg), _stream_handle(stream))
+    _check(rc, "tmfg_batch_run")
+    return outs
 
 
 def tmfg_sync_status(ctx: Context, stream=None, raise_on_error: bool = True) -> int:

@@ -50,6 +50,10 @@ struct tmfg_ctx {
     long long *stats;   // device [8]
     long long host_stats[16];
     unsigned long long timeout_ns;
+    void *stage;          // pinned host staging buffer for batch descriptor tables
+    size_t stage_bytes;
+    cudaEvent_t stage_ev; // recorded after the last copy out of the staging buffer
+    bool stage_used;
 };
 
 namespace {
@@ -178,6 +182,11 @@ int tmfg_create(tmfg_ctx **out, int device, size_t workspace_budget_bytes)
         delete c;
         return TMFG_ECUDA;
     }
+    if (cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaFree(c->status);
+        delete c;
+        return TMFG_ECUDA;
+    }
     c->timeout_ns = 60ull * 1000000000ull;
     if (const char *e = std::getenv("TMFG_TIMEOUT_MS")) {
         const long long ms = std::atoll(e);
@@ -194,6 +203,8 @@ void tmfg_destroy(tmfg_ctx *ctx)
     cudaDeviceSynchronize();
     if (ctx->work) cudaFree(ctx->work);
     if (ctx->status) cudaFree(ctx->status);
+    if (ctx->stage) cudaFreeHost(ctx->stage);
+    cudaEventDestroy(ctx->stage_ev);
     delete ctx;
 }
 
@@ -278,6 +289,193 @@ int tmfg_build(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, const tmfg_p
     a.stats = ctx->stats;
     a.timeout_ns = ctx->timeout_ns;
     return launch_loop(a, dtype, st);
+}
+
+int tmfg_batch_run(tmfg_ctx *ctx, const tmfg_job *jobs, int32_t count, const tmfg_params *params,
+                   const tmfg_batch_config *cfg, void *stream)
+{
+    if (!ctx || !jobs || count < 1 || !params) return TMFG_EINVAL;
+    const int dtype = params->dtype;
+    if (dtype != TMFG_F32 && dtype != TMFG_F64) return TMFG_EINVAL;
+    if (params->mode != TMFG_CORR && params->mode != TMFG_HEAP) return TMFG_EINVAL;
+    if (params->prefix < 1 || params->prefix > kMaxPrefixApi) return TMFG_EINVAL;
+    if (params->mode == TMFG_HEAP && params->prefix != 1) return TMFG_EINVAL;
+    const int sssp_threads = (cfg && cfg->sssp_threads) ? cfg->sssp_threads : 512;
+    if (sssp_threads != 256 && sssp_threads != 512) return TMFG_EINVAL;
+    const int64_t maxn_lib = tmfg_max_n(dtype);
+    int max_n = 0, napsp = 0;
+    for (int i = 0; i < count; ++i) {
+        const tmfg_job &J = jobs[i];
+        if (!J.S || J.n < 4 || J.ld < J.n || !J.order || !J.edges || !J.bubble_parent ||
+            (J.n > 4 && !J.ins_face) || (J.D && J.ldd < J.n))
+            return TMFG_EINVAL;
+        if (J.n > maxn_lib) return TMFG_ETOOBIG;
+        if (J.n > max_n) max_n = (int)J.n;
+        napsp += J.D != nullptr;
+    }
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return TMFG_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    // ---- sizes: descriptor tables, then per-instance blocks
+    const size_t t_sort = round256(sizeof(SortJob) * count);
+    const size_t t_rows = round256(sizeof(int) * (count + 1));
+    const size_t t_loop = round256(sizeof(LoopArgs) * count);
+    const size_t t_ajob = round256(sizeof(ApspJob) * (napsp + 1));
+    const size_t t_sarg = round256(sizeof(SsspArgs) * (napsp + 1));
+    const size_t t_ebeg = round256(sizeof(int) * (napsp + 1));
+    const size_t t_sbeg = round256(sizeof(int) * (napsp + 1));
+    const size_t tables = t_sort + t_rows + t_loop + t_ajob + t_sarg + t_ebeg + t_sbeg;
+    size_t build_bytes = 0, apsp_bytes = 0, deg_bytes = 0;
+    for (int i = 0; i < count; ++i) {
+        const int64_t n = jobs[i].n;
+        const size_t nf = 2 * (size_t)n - 4;
+        build_bytes += round256(2 * (size_t)n * (size_t)ldi_for(n)) + round256(8 * (size_t)n) +
+                       round256(16 * nf) * 4 + round256(8 * nf) + round256(4 * nf) + 256;
+        if (jobs[i].D) {
+            deg_bytes += 4 * (size_t)n;
+            apsp_bytes += round256(4 * ((size_t)n + 1)) + round256(4 * (size_t)n) +
+                          round256(8 * 2 * (3 * (size_t)n - 6));
+        }
+    }
+    deg_bytes = round256(deg_bytes);
+    const size_t total = tables + build_bytes + deg_bytes + apsp_bytes;
+    int rc = ensure_work(ctx, total, st);
+    if (rc) return rc;
+
+    // ---- host staging buffer (reused once its last copy has completed)
+    if (ctx->stage_used && cudaEventSynchronize(ctx->stage_ev) != cudaSuccess) return TMFG_ECUDA;
+    if (ctx->stage_bytes < tables) {
+        if (ctx->stage) cudaFreeHost(ctx->stage);
+        ctx->stage = nullptr;
+        ctx->stage_bytes = 0;
+        if (cudaHostAlloc(&ctx->stage, tables, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return TMFG_ENOMEM;
+        }
+        ctx->stage_bytes = tables;
+    }
+    char *hb = static_cast<char *>(ctx->stage);
+    char *db = static_cast<char *>(ctx->work);
+    SortJob *h_sort = reinterpret_cast<SortJob *>(hb);
+    int *h_rows = reinterpret_cast<int *>(hb + t_sort);
+    LoopArgs *h_loop = reinterpret_cast<LoopArgs *>(hb + t_sort + t_rows);
+    ApspJob *h_ajob = reinterpret_cast<ApspJob *>(hb + t_sort + t_rows + t_loop);
+    SsspArgs *h_sarg = reinterpret_cast<SsspArgs *>(hb + t_sort + t_rows + t_loop + t_ajob);
+    int *h_ebeg = reinterpret_cast<int *>(hb + t_sort + t_rows + t_loop + t_ajob + t_sarg);
+    int *h_sbeg = reinterpret_cast<int *>(hb + t_sort + t_rows + t_loop + t_ajob + t_sarg + t_ebeg);
+    const SortJob *d_sort = reinterpret_cast<const SortJob *>(db);
+    const int *d_rows = reinterpret_cast<const int *>(db + t_sort);
+    const LoopArgs *d_loop = reinterpret_cast<const LoopArgs *>(db + t_sort + t_rows);
+    const ApspJob *d_ajob = reinterpret_cast<const ApspJob *>(db + t_sort + t_rows + t_loop);
+    const SsspArgs *d_sarg = reinterpret_cast<const SsspArgs *>(db + t_sort + t_rows + t_loop + t_ajob);
+    const int *d_ebeg = reinterpret_cast<const int *>(db + t_sort + t_rows + t_loop + t_ajob + t_sarg);
+    const int *d_sbeg = reinterpret_cast<const int *>(db + t_sort + t_rows + t_loop + t_ajob + t_sarg + t_ebeg);
+
+    char *p = db + tables;
+    char *deg = p + build_bytes;
+    char *ap = deg + deg_bytes;
+    auto take = [&](char *&q, size_t x) { void *r = q; q += round256(x); return r; };
+    int row_acc = 0, edge_acc = 0, src_acc = 0, a = 0;
+    size_t deg_off = 0;
+    for (int i = 0; i < count; ++i) {
+        const tmfg_job &J = jobs[i];
+        const int n = (int)J.n;
+        const size_t nf = 2 * (size_t)n - 4;
+        const long long ldi = ldi_for(n);
+        uint16_t *idx = static_cast<uint16_t *>(take(p, 2 * (size_t)n * (size_t)ldi));
+        long long *rowsum = static_cast<long long *>(take(p, 8 * (size_t)n));
+        int4 *face = static_cast<int4 *>(take(p, 16 * nf));
+        void *lf = take(p, 16 * nf);
+        void *ls = take(p, 16 * nf);
+        void *pk = take(p, 16 * nf);
+        unsigned long long *pc = static_cast<unsigned long long *>(take(p, 8 * nf));
+        int *fu = static_cast<int *>(take(p, 4 * nf));
+        long long *stats = static_cast<long long *>(take(p, 128));
+        SortJob &sj = h_sort[i];
+        sj.S = J.S;
+        sj.ld = J.ld;
+        sj.n = n;
+        sj.vec_in = (J.ld % (dtype == TMFG_F32 ? 4 : 2) == 0) && ((uintptr_t)J.S % 16 == 0);
+        sj.vec_out = true;
+        sj.idx = idx;
+        sj.ldi = ldi;
+        sj.rowsum = rowsum;
+        h_rows[i] = row_acc;
+        row_acc += n;
+        LoopArgs &la = h_loop[i];
+        la = LoopArgs{};
+        la.S = J.S;
+        la.ld = J.ld;
+        la.n = n;
+        la.mode = params->mode;
+        la.P = params->prefix;
+        la.idx = idx;
+        la.ldi = ldi;
+        la.rowsum = rowsum;
+        la.order = J.order;
+        la.edges = J.edges;
+        la.ins_face = J.ins_face;
+        la.parent = J.bubble_parent;
+        la.face = face;
+        la.leaf_fresh = lf;
+        la.leaf_stale = ls;
+        la.pend_key = pk;
+        la.pend_cand = pc;
+        la.fu_buf = fu;
+        la.status = ctx->status;
+        la.stats = stats;
+        la.timeout_ns = ctx->timeout_ns;
+        la.state = nullptr;
+        la.k_stop = n - 4;
+        la.resume = 0;
+        if (J.D) {
+            ApspJob &aj = h_ajob[a];
+            aj.S = J.S;
+            aj.ld = J.ld;
+            aj.n = n;
+            aj.edges = J.edges;
+            aj.deg = reinterpret_cast<int *>(deg + deg_off);
+            deg_off += 4 * (size_t)n;
+            aj.rowptr = static_cast<int *>(take(ap, 4 * ((size_t)n + 1)));
+            aj.cursor = static_cast<int *>(take(ap, 4 * (size_t)n));
+            aj.arcs = static_cast<uint2 *>(take(ap, 8 * 2 * (3 * (size_t)n - 6)));
+            SsspArgs &sa = h_sarg[a];
+            sa = SsspArgs{};
+            sa.n = n;
+            sa.rowptr = aj.rowptr;
+            sa.arcs = aj.arcs;
+            sa.src = nullptr;
+            sa.nsrc = n;
+            sa.out = J.D;
+            sa.ldo = J.ldd;
+            sa.status = ctx->status;
+            sa.timeout_ns = ctx->timeout_ns;
+            h_ebeg[a] = edge_acc;
+            h_sbeg[a] = src_acc;
+            edge_acc += 3 * n - 6;
+            src_acc += n;
+            ++a;
+        }
+    }
+    h_rows[count] = row_acc;
+    h_ebeg[napsp] = edge_acc;
+    h_sbeg[napsp] = src_acc;
+    if (cudaMemcpyAsync(db, hb, tables, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaEventRecord(ctx->stage_ev, st) != cudaSuccess)
+        return TMFG_ECUDA;
+    ctx->stage_used = true;
+    if (napsp && cudaMemsetAsync(deg, 0, deg_bytes, st) != cudaSuccess) return TMFG_ECUDA;
+
+    rc = launch_rowsort_batch(d_sort, d_rows, count, max_n, dtype, ctx->status,
+                              ctx->num_sms * 2, st);
+    if (rc) return rc;
+    rc = launch_loop_batch(d_loop, count, max_n, dtype, params->mode, st);
+    if (rc) return rc;
+    if (napsp)
+        rc = launch_apsp_batch(d_ajob, d_sarg, d_ebeg, d_sbeg, napsp, edge_acc, max_n, dtype,
+                               sssp_threads, ctx->status, ctx->num_sms, st);
+    return rc;
 }
 
 int tmfg_apsp(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, int32_t dtype,

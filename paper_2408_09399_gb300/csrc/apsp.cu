@@ -28,7 +28,7 @@
 
 namespace tmfg {
 
-constexpr int kSsspThreads = 512;
+constexpr int kSsspThreads = 512;  // default CTA size of the SSSP kernels
 
 // ------------------------------------------------------------------ CSR
 __global__ void csr_degree_kernel(const int *__restrict__ edges, int ne, int n, int *deg,
@@ -117,31 +117,21 @@ __global__ void csr_fill_kernel(const int *__restrict__ edges, int ne, int n,
 }
 
 // ----------------------------------------------------------------- SSSP
-struct SsspArgs {
-    int n;
-    const int *rowptr;
-    const uint2 *arcs;
-    const int *src;      // sources (null: source i = i)
-    int nsrc;
-    float *out;          // row i of the output = source src[i]
-    long long ldo;
-    // approximate form
-    const float *dnear;  // [n] distance to the nearest hub
-    const int *near;     // [n] rank of the nearest hub
-    const float *DH;     // [h x n] exact hub rows
-    float rf;            // radius factor
-    int *status;
-    unsigned long long timeout_ns;
-};
 
 // Shared memory: dist[n] floats, two frontier bitmaps, a frontier list of at
 // most list_cap ids, and a list of high-degree frontier vertices.
-__host__ __device__ inline int sssp_list_cap(int n) { return ((n / 2) + 15) & ~15; }
+// at least 32 entries, so that any one bitmap word fits an empty window
+__host__ __device__ inline int sssp_list_cap(int n)
+{
+    return (((n / 2) > 32 ? (n / 2) : 32) + 15) & ~15;
+}
 constexpr int kHeavyCap = 512;
 constexpr int kHeavyDeg = 16;
 
-template <bool kBounded>
-__global__ void __launch_bounds__(kSsspThreads, 2) sssp_kernel(SsspArgs a)
+// Single-source search for source index i of a (row i of a.out).  Returns
+// false when the run must stop (an earlier error or the time limit).
+template <bool kBounded, int NT>
+__device__ __forceinline__ bool sssp_source(const SsspArgs &a, int i, uint64_t t0)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_cnt, s_listed, s_hcnt, s_abort, s_wnext;
@@ -153,18 +143,16 @@ __global__ void __launch_bounds__(kSsspThreads, 2) sssp_kernel(SsspArgs a)
     uint32_t *bm1 = bm0 + W;
     uint16_t *list = reinterpret_cast<uint16_t *>(bm1 + W);
     uint16_t *heavy = list + cap;
-    const uint64_t t0 = globaltimer_ns();
-
-    for (int i = blockIdx.x; i < a.nsrc; i += gridDim.x) {
+    {
         if (tid == 0) s_abort = (*(volatile int *)a.status != 0) ||
                                 (globaltimer_ns() - t0 > a.timeout_ns);
         const int s = a.src ? a.src[i] : i;
-        for (int v = tid; v < n; v += kSsspThreads) dist[v] = __int_as_float(0x7f800000);
-        for (int w = tid; w < W; w += kSsspThreads) { bm0[w] = 0; bm1[w] = 0; }
+        for (int v = tid; v < n; v += NT) dist[v] = __int_as_float(0x7f800000);
+        for (int w = tid; w < W; w += NT) { bm0[w] = 0; bm1[w] = 0; }
         __syncthreads();
         if (s_abort) {
             if (tid == 0 && *(volatile int *)a.status == 0) set_status(a.status, TMFG_ETIMEOUT);
-            return;
+            return false;
         }
         const float r = kBounded ? __fmul_rn(a.rf, a.dnear[s]) : __int_as_float(0x7f800000);
         if (tid == 0) {
@@ -182,7 +170,7 @@ __global__ void __launch_bounds__(kSsspThreads, 2) sssp_kernel(SsspArgs a)
             while (wstart < W) {
                 if (tid == 0) { s_cnt = 0; s_listed = 0; s_hcnt = 0; s_wnext = W; }
                 __syncthreads();
-                for (int w = wstart + tid; w < W; w += kSsspThreads) {
+                for (int w = wstart + tid; w < W; w += NT) {
                     uint32_t b = cur[w];
                     if (!b) continue;
                     const int c = __popc(b);
@@ -206,8 +194,12 @@ __global__ void __launch_bounds__(kSsspThreads, 2) sssp_kernel(SsspArgs a)
                 const int cnt = s_listed;
                 const int wn = s_wnext;
                 any |= cnt > 0;
+                if (cnt == 0 && wn < W) {  // no progress is impossible; stop rather than spin
+                    if (tid == 0) set_status(a.status, TMFG_EINTERNAL);
+                    return false;
+                }
                 // relax: light vertices one per thread, heavy ones a warp each
-                for (int j = tid; j < cnt; j += kSsspThreads) {
+                for (int j = tid; j < cnt; j += NT) {
                     const int u = list[j];
                     if (u >= n) continue;
                     const float du = dist[u];
@@ -240,7 +232,7 @@ __global__ void __launch_bounds__(kSsspThreads, 2) sssp_kernel(SsspArgs a)
                 }
                 __syncthreads();
                 const int hc = s_hcnt < kHeavyCap ? s_hcnt : kHeavyCap;
-                for (int j = warp; j < hc; j += kSsspThreads / 32) {
+                for (int j = warp; j < hc; j += NT / 32) {
                     const int u = heavy[j];
                     const float du = dist[u];
                     const int p1 = a.rowptr[u + 1];
@@ -271,17 +263,17 @@ __global__ void __launch_bounds__(kSsspThreads, 2) sssp_kernel(SsspArgs a)
         if (!kBounded) {
             if (vec) {
                 const int n4 = n >> 2;
-                for (int q = tid; q < n4; q += kSsspThreads)
+                for (int q = tid; q < n4; q += NT)
                     __stcs(reinterpret_cast<float4 *>(orow) + q,
                            make_float4(dist[4 * q], dist[4 * q + 1], dist[4 * q + 2], dist[4 * q + 3]));
-                for (int t = 4 * n4 + tid; t < n; t += kSsspThreads) orow[t] = dist[t];
+                for (int t = 4 * n4 + tid; t < n; t += NT) orow[t] = dist[t];
             } else {
-                for (int t = tid; t < n; t += kSsspThreads) orow[t] = dist[t];
+                for (int t = tid; t < n; t += NT) orow[t] = dist[t];
             }
         } else {
             const float ds = a.dnear[s];
             const float *hrow = a.DH + (long long)a.near[s] * n;
-            for (int t = tid; t < n; t += kSsspThreads) {
+            for (int t = tid; t < n; t += NT) {
                 const float es = __fadd_rn(ds, hrow[t]);
                 const float et = __fadd_rn(a.dnear[t], a.DH[(long long)a.near[t] * n + s]);
                 float v = fminf(es, et);
@@ -291,6 +283,37 @@ __global__ void __launch_bounds__(kSsspThreads, 2) sssp_kernel(SsspArgs a)
             }
         }
         __syncthreads();
+    }
+    return true;
+}
+
+template <bool kBounded, int NT>
+__global__ void __launch_bounds__(NT, 2) sssp_kernel(SsspArgs a)
+{
+    const uint64_t t0 = globaltimer_ns();
+    for (int i = blockIdx.x; i < a.nsrc; i += gridDim.x)
+        if (!sssp_source<kBounded, NT>(a, i, t0)) return;
+}
+
+// Many graphs: source g of the launch is source g - src_begin[j] of job j.
+template <int NT>
+__global__ void __launch_bounds__(NT, 2) sssp_batch_kernel(const SsspArgs *__restrict__ args,
+                                                           const int *__restrict__ src_begin,
+                                                           int njobs)
+{
+    __shared__ SsspArgs s_a;
+    const uint64_t t0 = globaltimer_ns();
+    const int total = src_begin[njobs];
+    for (int g = blockIdx.x; g < total; g += gridDim.x) {
+        int lo = 0, hi = njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (src_begin[mid] <= g) lo = mid; else hi = mid - 1;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_a = args[lo];
+        __syncthreads();
+        if (!sssp_source<false, NT>(s_a, g - src_begin[lo], t0)) return;
     }
 }
 
@@ -483,9 +506,9 @@ int launch_apsp(const void *S, int n, long long ld, int dtype, const int *edges,
                                                         w.cursor, w.arcs);
     const size_t smem = sssp_smem_bytes(n);
     if (smem > 232448) return TMFG_ETOOBIG;
-    if (cudaFuncSetAttribute(sssp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(sssp_kernel<false, kSsspThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess ||
-        cudaFuncSetAttribute(sssp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(sssp_kernel<true, kSsspThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return TMFG_ECUDA;
     SsspArgs a{};
@@ -500,7 +523,7 @@ int launch_apsp(const void *S, int n, long long ld, int dtype, const int *edges,
         a.out = D;
         a.ldo = ldd;
         const int grid = n < 2 * num_sms ? n : 2 * num_sms;
-        sssp_kernel<false><<<grid, kSsspThreads, smem, stream>>>(a);
+        sssp_kernel<false, kSsspThreads><<<grid, kSsspThreads, smem, stream>>>(a);
         return cudaGetLastError() == cudaSuccess ? TMFG_OK : TMFG_ECUDA;
     }
     // hubs and their exact rows
@@ -514,7 +537,7 @@ int launch_apsp(const void *S, int n, long long ld, int dtype, const int *edges,
     a.nsrc = h;
     a.out = w.DH;
     a.ldo = n;
-    sssp_kernel<false><<<h < 2 * num_sms ? h : 2 * num_sms, kSsspThreads, smem, stream>>>(a);
+    sssp_kernel<false, kSsspThreads><<<h < 2 * num_sms ? h : 2 * num_sms, kSsspThreads, smem, stream>>>(a);
     nearest_hub_kernel<<<(n + 255) / 256, 256, 0, stream>>>(w.DH, h, n, w.near, w.dnear);
     // bounded search from every vertex, approximate rows, then min with the transpose
     a.src = nullptr;
@@ -525,10 +548,134 @@ int launch_apsp(const void *S, int n, long long ld, int dtype, const int *edges,
     a.near = w.near;
     a.DH = w.DH;
     a.rf = rf;
-    sssp_kernel<true><<<n < 2 * num_sms ? n : 2 * num_sms, kSsspThreads, smem, stream>>>(a);
+    sssp_kernel<true, kSsspThreads><<<n < 2 * num_sms ? n : 2 * num_sms, kSsspThreads, smem, stream>>>(a);
     const int T = (n + 31) / 32;
     sym_min_kernel<<<dim3(T, T), dim3(32, 8), 0, stream>>>(D, ldd, n);
     return cudaGetLastError() == cudaSuccess ? TMFG_OK : TMFG_ECUDA;
+}
+
+}  // namespace tmfg
+
+// ------------------------------------------------------------ batched
+namespace tmfg {
+
+// Exact APSP of many graphs at once: the CSR of every job is built by
+// kernels over the concatenated edge lists, then one persistent grid runs a
+// search per (job, source) pair.
+
+__device__ __forceinline__ int find_job(const int *__restrict__ begin, int njobs, int x)
+{
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (begin[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void csr_degree_batch_kernel(const ApspJob *__restrict__ jobs,
+                                        const int *__restrict__ edge_begin, int njobs, int *status)
+{
+    const int total = edge_begin[njobs];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int j = find_job(edge_begin, njobs, e);
+        const ApspJob &J = jobs[j];
+        const int le = e - edge_begin[j];
+        const int a = J.edges[2 * le], b = J.edges[2 * le + 1];
+        if (a < 0 || b < 0 || a >= J.n || b >= J.n || a == b) {
+            set_status(status, TMFG_EINVAL);
+            continue;
+        }
+        atomicAdd(&J.deg[a], 1);
+        atomicAdd(&J.deg[b], 1);
+    }
+}
+
+// one CTA per job: row pointers and fill cursors from the degrees
+__global__ void __launch_bounds__(1024) csr_scan_batch_kernel(const ApspJob *__restrict__ jobs)
+{
+    const ApspJob &J = jobs[blockIdx.x];
+    __shared__ int wsum[32];
+    const int n = J.n;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int per = (n + 1023) / 1024;
+    const int lo = t * per, hi = min(n, lo + per);
+    int sum = 0;
+    for (int v = lo; v < hi; ++v) sum += J.deg[v];
+    int x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const int w = wsum[lane];
+        int z = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
+        }
+        wsum[lane] = z - w;
+    }
+    __syncthreads();
+    int run = wsum[warp] + x - sum;
+    if (t == 0) J.rowptr[0] = 0;
+    for (int v = lo; v < hi; ++v) {
+        J.cursor[v] = run;
+        run += J.deg[v];
+        J.rowptr[v + 1] = run;
+    }
+}
+
+template <typename T>
+__global__ void csr_fill_batch_kernel(const ApspJob *__restrict__ jobs,
+                                      const int *__restrict__ edge_begin, int njobs)
+{
+    const int total = edge_begin[njobs];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int j = find_job(edge_begin, njobs, e);
+        const ApspJob &J = jobs[j];
+        const int le = e - edge_begin[j];
+        const int a = J.edges[2 * le], b = J.edges[2 * le + 1];
+        if (a < 0 || b < 0 || a >= J.n || b >= J.n || a == b) continue;
+        const T *S = static_cast<const T *>(J.S);
+        const float l = edge_length<T>(canon(S[(long long)a * J.ld + b]));
+        const int pa = atomicAdd(&J.cursor[a], 1);
+        const int pb = atomicAdd(&J.cursor[b], 1);
+        J.arcs[pa] = make_uint2((unsigned)b, __float_as_uint(l));
+        J.arcs[pb] = make_uint2((unsigned)a, __float_as_uint(l));
+    }
+}
+
+// d_jobs / d_sargs: device copies of the job and SSSP tables; edge_begin and
+// src_begin: device prefix sums (njobs + 1).  The degree arrays of every job
+// must be zero on entry.
+int launch_apsp_batch(const ApspJob *d_jobs, const SsspArgs *d_sargs, const int *d_edge_begin,
+                      const int *d_src_begin, int njobs, int total_edges, int max_n, int dtype,
+                      int sssp_threads, int *status, int num_sms, cudaStream_t stream)
+{
+    const int eb = (total_edges + 255) / 256;
+    const int egrid = eb < 8 * num_sms ? (eb > 0 ? eb : 1) : 8 * num_sms;
+    csr_degree_batch_kernel<<<egrid, 256, 0, stream>>>(d_jobs, d_edge_begin, njobs, status);
+    csr_scan_batch_kernel<<<njobs, 1024, 0, stream>>>(d_jobs);
+    if (dtype == TMFG_F32)
+        csr_fill_batch_kernel<float><<<egrid, 256, 0, stream>>>(d_jobs, d_edge_begin, njobs);
+    else
+        csr_fill_batch_kernel<double><<<egrid, 256, 0, stream>>>(d_jobs, d_edge_begin, njobs);
+    const size_t smem = sssp_smem_bytes(max_n);
+    if (smem > kSmemLimit) return TMFG_ETOOBIG;
+    auto go = [&](auto k, int nt) {
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return (int)TMFG_ECUDA;
+        k<<<2 * num_sms, nt, smem, stream>>>(d_sargs, d_src_begin, njobs);
+        return cudaGetLastError() == cudaSuccess ? (int)TMFG_OK : (int)TMFG_ECUDA;
+    };
+    if (sssp_threads == 256) return go(sssp_batch_kernel<256>, 256);
+    return go(sssp_batch_kernel<512>, 512);
 }
 
 }  // namespace tmfg

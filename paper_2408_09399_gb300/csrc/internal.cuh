@@ -6,7 +6,19 @@
 namespace tmfg {
 
 // rowsort.cu
+struct SortJob {  // the rows of one matrix, for the batched sort
+    const void *S;
+    long long ld;
+    int n;
+    bool vec_in, vec_out;
+    uint16_t *idx;
+    long long ldi;
+    long long *rowsum;
+};
 int64_t rowsort_max_n(int dtype);
+size_t rowsort_smem(int n, int dtype);
+int launch_rowsort_batch(const SortJob *d_jobs, const int *d_row_begin, int njobs, int max_n,
+                         int dtype, int *status, int grid, cudaStream_t stream);
 int launch_rowsort(const void *S, int n, long long ld, int dtype, uint16_t *idx, long long ldi,
                    long long *rowsum, int *status, int num_sms, cudaStream_t stream);
 
@@ -40,8 +52,37 @@ struct LoopArgs {
 size_t loop_smem_bytes(int n, int dtype, int mode);
 size_t loop_state_bytes(int n);
 int launch_loop(const LoopArgs &args, int dtype, cudaStream_t stream);
+int launch_loop_batch(const LoopArgs *d_args, int count, int max_n, int dtype, int mode,
+                      cudaStream_t stream);
 
 // apsp.cu
+struct SsspArgs {
+    int n;
+    const int *rowptr;
+    const uint2 *arcs;
+    const int *src;      // sources (null: source i = i)
+    int nsrc;
+    float *out;          // row i of the output = source src[i]
+    long long ldo;
+    // approximate form
+    const float *dnear;  // [n] distance to the nearest hub
+    const int *near;     // [n] rank of the nearest hub
+    const float *DH;     // [h x n] exact hub rows
+    float rf;            // radius factor
+    int *status;
+    unsigned long long timeout_ns;
+};
+struct ApspJob {  // one graph of a batched exact APSP
+    const void *S;
+    long long ld;
+    int n;
+    const int *edges;
+    int *deg, *rowptr, *cursor;
+    uint2 *arcs;
+};
+int launch_apsp_batch(const ApspJob *d_jobs, const SsspArgs *d_sargs, const int *d_edge_begin,
+                      const int *d_src_begin, int njobs, int total_edges, int max_n, int dtype,
+                      int sssp_threads, int *status, int num_sms, cudaStream_t stream);
 size_t apsp_work_bytes(int n, int approx, int h);
 size_t sssp_smem_bytes(int n);
 int launch_apsp(const void *S, int n, long long ld, int dtype, const int *edges, int approx,

@@ -18,6 +18,8 @@
 //   * the sorted positions are converted to vertex ids (skipping the
 //     diagonal) and written with 16-byte stores, rows padded to ldi with
 //     0xFFFF.
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace tmfg {
@@ -163,13 +165,13 @@ __device__ __forceinline__ void store_row(const uint16_t *pos, int m, int v, uin
 }
 
 // ---------------------------------------------------------------- float rows
+// Sort row v of an n x n float matrix (row = S + v*ld) into out (ldi ids).
 template <int I>
-__global__ void __launch_bounds__(kSortThreads, 1)
-rowsort_f32_kernel(const float *__restrict__ S, int n, long long ld, bool vec_in,
-                   uint16_t *__restrict__ idx, long long ldi, bool vec_out,
-                   long long *__restrict__ rowsum, int *status)
+__device__ __forceinline__ void sort_row_f32(const float *__restrict__ row, int n, int v,
+                                             bool vec_in, uint16_t *__restrict__ out,
+                                             long long ldi, bool vec_out, long long *rowsum_v,
+                                             int *status, unsigned char *smem)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
     const int m = n - 1;
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
     uint32_t *wsum = reinterpret_cast<uint32_t *>(smem + kHistBytes);
@@ -184,63 +186,59 @@ rowsort_f32_kernel(const float *__restrict__ S, int n, long long ld, bool vec_in
     uint16_t *p1v = reinterpret_cast<uint16_t *>(r2 + 4 * (size_t)m);
     uint32_t *p3 = reinterpret_cast<uint32_t *>(r2);
 
-    for (int v = blockIdx.x; v < n; v += gridDim.x) {
-        const float *row = S + (long long)v * ld;
-        long long acc = 0;
-        int bad = 0;
-        auto take = [&](int u, float x) {
-            if (u == v) return;
-            x = canon(x);
-            int c = check_entry(x);
-            if (c) bad = c;
-            acc += quantize40(x);
-            key0[u - (u > v)] = ~ord_key(x);  // ascending key = descending S
-        };
-        if (vec_in) {
-            const int n4 = n >> 2;
-            const float4 *row4 = reinterpret_cast<const float4 *>(row);
-            for (int q = threadIdx.x; q < n4; q += blockDim.x) {
-                float4 x = __ldcs(row4 + q);
-                take(4 * q, x.x);
-                take(4 * q + 1, x.y);
-                take(4 * q + 2, x.z);
-                take(4 * q + 3, x.w);
-            }
-            for (int u = 4 * n4 + threadIdx.x; u < n; u += blockDim.x) take(u, row[u]);
-        } else {
-            for (int u = threadIdx.x; u < n; u += blockDim.x) take(u, row[u]);
+    long long acc = 0;
+    int bad = 0;
+    auto take = [&](int u, float x) {
+        if (u == v) return;
+        x = canon(x);
+        int c = check_entry(x);
+        if (c) bad = c;
+        acc += quantize40(x);
+        key0[u - (u > v)] = ~ord_key(x);  // ascending key = descending S
+    };
+    if (vec_in) {
+        const int n4 = n >> 2;
+        const float4 *row4 = reinterpret_cast<const float4 *>(row);
+        for (int q = threadIdx.x; q < n4; q += blockDim.x) {
+            float4 x = __ldcs(row4 + q);
+            take(4 * q, x.x);
+            take(4 * q + 1, x.y);
+            take(4 * q + 2, x.z);
+            take(4 * q + 3, x.w);
         }
-        if (bad) set_status(status, bad);
-        __syncthreads();
-        const long long rs = block_sum_ll(acc, red);
-        if (threadIdx.x == 0 && rowsum) rowsum[v] = rs;
-
-        radix_pass<I>(m, hist, wsum,
-            [&](int p) { return key0[p] & 0xFFu; },
-            [&](int p, uint32_t q) { p1k[q] = key0[p] >> 8; p1v[q] = (uint16_t)p; });
-        radix_pass<I>(m, hist, wsum,
-            [&](int p) { return p1k[p] & 0xFFu; },
-            [&](int p, uint32_t q) { p2[q] = ((p1k[p] >> 8) << 16) | p1v[p]; });
-        radix_pass<I>(m, hist, wsum,
-            [&](int p) { return (p2[p] >> 16) & 0xFFu; },
-            [&](int p, uint32_t q) { p3[q] = ((p2[p] >> 24) << 16) | (p2[p] & 0xFFFFu); });
-        radix_pass<I>(m, hist, wsum,
-            [&](int p) { return p3[p] >> 16; },
-            [&](int p, uint32_t q) { out16[q] = (uint16_t)(p3[p] & 0xFFFFu); });
-
-        store_row(out16, m, v, idx + (long long)v * ldi, ldi, vec_out);
-        __syncthreads();
+        for (int u = 4 * n4 + threadIdx.x; u < n; u += blockDim.x) take(u, row[u]);
+    } else {
+        for (int u = threadIdx.x; u < n; u += blockDim.x) take(u, row[u]);
     }
+    if (bad) set_status(status, bad);
+    __syncthreads();
+    const long long rs = block_sum_ll(acc, red);
+    if (threadIdx.x == 0 && rowsum_v) *rowsum_v = rs;
+
+    radix_pass<I>(m, hist, wsum,
+        [&](int p) { return key0[p] & 0xFFu; },
+        [&](int p, uint32_t q) { p1k[q] = key0[p] >> 8; p1v[q] = (uint16_t)p; });
+    radix_pass<I>(m, hist, wsum,
+        [&](int p) { return p1k[p] & 0xFFu; },
+        [&](int p, uint32_t q) { p2[q] = ((p1k[p] >> 8) << 16) | p1v[p]; });
+    radix_pass<I>(m, hist, wsum,
+        [&](int p) { return (p2[p] >> 16) & 0xFFu; },
+        [&](int p, uint32_t q) { p3[q] = ((p2[p] >> 24) << 16) | (p2[p] & 0xFFFFu); });
+    radix_pass<I>(m, hist, wsum,
+        [&](int p) { return p3[p] >> 16; },
+        [&](int p, uint32_t q) { out16[q] = (uint16_t)(p3[p] & 0xFFFFu); });
+
+    store_row(out16, m, v, out, ldi, vec_out);
+    __syncthreads();
 }
 
 // --------------------------------------------------------------- double rows
 template <int I>
-__global__ void __launch_bounds__(kSortThreads, 1)
-rowsort_f64_kernel(const double *__restrict__ S, int n, long long ld, bool vec_in,
-                   uint16_t *__restrict__ idx, long long ldi, bool vec_out,
-                   long long *__restrict__ rowsum, int *status)
+__device__ __forceinline__ void sort_row_f64(const double *__restrict__ row, int n, int v,
+                                             bool vec_in, uint16_t *__restrict__ out,
+                                             long long ldi, bool vec_out, long long *rowsum_v,
+                                             int *status, unsigned char *smem)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
     const int m = n - 1;
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
     uint32_t *wsum = reinterpret_cast<uint32_t *>(smem + kHistBytes);
@@ -251,61 +249,109 @@ rowsort_f64_kernel(const double *__restrict__ S, int n, long long ld, bool vec_i
     uint16_t *v0 = reinterpret_cast<uint16_t *>(k1 + m);
     uint16_t *v1 = v0 + m;
 
-    for (int v = blockIdx.x; v < n; v += gridDim.x) {
-        const double *row = S + (long long)v * ld;
-        long long acc = 0;
-        int bad = 0;
-        auto take = [&](int u, double x) {
-            if (u == v) return;
-            x = canon(x);
-            int c = check_entry(x);
-            if (c) bad = c;
-            acc += quantize40(x);
-            k0[u - (u > v)] = ~ord_key(x);
-        };
-        if (vec_in) {
-            const int n2 = n >> 1;
-            const double2 *row2 = reinterpret_cast<const double2 *>(row);
-            for (int q = threadIdx.x; q < n2; q += blockDim.x) {
-                double2 x = __ldcs(row2 + q);
-                take(2 * q, x.x);
-                take(2 * q + 1, x.y);
-            }
-            for (int u = 2 * n2 + threadIdx.x; u < n; u += blockDim.x) take(u, row[u]);
-        } else {
-            for (int u = threadIdx.x; u < n; u += blockDim.x) take(u, row[u]);
+    long long acc = 0;
+    int bad = 0;
+    auto take = [&](int u, double x) {
+        if (u == v) return;
+        x = canon(x);
+        int c = check_entry(x);
+        if (c) bad = c;
+        acc += quantize40(x);
+        k0[u - (u > v)] = ~ord_key(x);
+    };
+    if (vec_in) {
+        const int n2 = n >> 1;
+        const double2 *row2 = reinterpret_cast<const double2 *>(row);
+        for (int q = threadIdx.x; q < n2; q += blockDim.x) {
+            double2 x = __ldcs(row2 + q);
+            take(2 * q, x.x);
+            take(2 * q + 1, x.y);
         }
-        if (bad) set_status(status, bad);
-        __syncthreads();
-        const long long rs = block_sum_ll(acc, red);
-        if (threadIdx.x == 0 && rowsum) rowsum[v] = rs;
+        for (int u = 2 * n2 + threadIdx.x; u < n; u += blockDim.x) take(u, row[u]);
+    } else {
+        for (int u = threadIdx.x; u < n; u += blockDim.x) take(u, row[u]);
+    }
+    if (bad) set_status(status, bad);
+    __syncthreads();
+    const long long rs = block_sum_ll(acc, red);
+    if (threadIdx.x == 0 && rowsum_v) *rowsum_v = rs;
 
-        // pass 0: positions are implicit
-        radix_pass<I>(m, hist, wsum,
-            [&](int p) { return (uint32_t)(k0[p] & 0xFFu); },
-            [&](int p, uint32_t q) { k1[q] = k0[p]; v1[q] = (uint16_t)p; });
+    // pass 0: positions are implicit
+    radix_pass<I>(m, hist, wsum,
+        [&](int p) { return (uint32_t)(k0[p] & 0xFFu); },
+        [&](int p, uint32_t q) { k1[q] = k0[p]; v1[q] = (uint16_t)p; });
 #pragma unroll 1
-        for (int pass = 1; pass < 8; ++pass) {
-            const int sh = 8 * pass;
-            uint64_t *ks = (pass & 1) ? k1 : k0;
-            uint64_t *kd = (pass & 1) ? k0 : k1;
-            uint16_t *vs = (pass & 1) ? v1 : v0;
-            uint16_t *vd = (pass & 1) ? v0 : v1;
-            radix_pass<I>(m, hist, wsum,
-                [&](int p) { return (uint32_t)((ks[p] >> sh) & 0xFFu); },
-                [&](int p, uint32_t q) { kd[q] = ks[p]; vd[q] = vs[p]; });
+    for (int pass = 1; pass < 8; ++pass) {
+        const int sh = 8 * pass;
+        uint64_t *ks = (pass & 1) ? k1 : k0;
+        uint64_t *kd = (pass & 1) ? k0 : k1;
+        uint16_t *vs = (pass & 1) ? v1 : v0;
+        uint16_t *vd = (pass & 1) ? v0 : v1;
+        radix_pass<I>(m, hist, wsum,
+            [&](int p) { return (uint32_t)((ks[p] >> sh) & 0xFFu); },
+            [&](int p, uint32_t q) { kd[q] = ks[p]; vd[q] = vs[p]; });
+    }
+    // after 8 passes the result is in (k0, v0)
+    store_row(v0, m, v, out, ldi, vec_out && ((uintptr_t)v0 % 16 == 0));
+    __syncthreads();
+}
+
+template <int I, typename T>
+__device__ __forceinline__ void sort_row(const T *row, int n, int v, bool vec_in, uint16_t *out,
+                                         long long ldi, bool vec_out, long long *rowsum_v,
+                                         int *status, unsigned char *smem)
+{
+    if constexpr (sizeof(T) == 4)
+        sort_row_f32<I>(row, n, v, vec_in, out, ldi, vec_out, rowsum_v, status, smem);
+    else
+        sort_row_f64<I>(row, n, v, vec_in, out, ldi, vec_out, rowsum_v, status, smem);
+}
+
+// One matrix: a persistent grid walks its rows.
+template <int I, typename T>
+__global__ void __launch_bounds__(kSortThreads, 1)
+rowsort_kernel(const T *__restrict__ S, int n, long long ld, bool vec_in, uint16_t *__restrict__ idx,
+               long long ldi, bool vec_out, long long *__restrict__ rowsum, int *status)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int v = blockIdx.x; v < n; v += gridDim.x)
+        sort_row<I, T>(S + (long long)v * ld, n, v, vec_in, idx + (long long)v * ldi, ldi, vec_out,
+                       rowsum ? rowsum + v : nullptr, status, smem);
+}
+
+// Many matrices: a persistent grid walks the rows of all jobs (row r of the
+// launch is row r - row_begin[j] of job j).
+template <int I, typename T>
+__global__ void __launch_bounds__(kSortThreads, 1)
+rowsort_batch_kernel(const SortJob *__restrict__ jobs, const int *__restrict__ row_begin, int njobs,
+                     int *status)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int total = row_begin[njobs];
+    for (int r = blockIdx.x; r < total; r += gridDim.x) {
+        int lo = 0, hi = njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (row_begin[mid] <= r) lo = mid; else hi = mid - 1;
         }
-        // after 8 passes the result is in (k0, v0)
-        store_row(v0, m, v, idx + (long long)v * ldi, ldi, vec_out && ((uintptr_t)v0 % 16 == 0));
-        __syncthreads();
+        const SortJob &J = jobs[lo];
+        const int v = r - row_begin[lo];
+        const T *S = static_cast<const T *>(J.S);
+        sort_row<I, T>(S + (long long)v * J.ld, J.n, v, J.vec_in, J.idx + (long long)v * J.ldi,
+                       J.ldi, J.vec_out, J.rowsum ? J.rowsum + v : nullptr, status, smem);
     }
 }
 
 // ------------------------------------------------------------------- launch
-static int pick_items(int m, const int *choices, int nc)
+static const int kItemsF32[] = {1, 2, 4, 8, 16, 24, 32, 43};
+static const int kItemsF64[] = {1, 2, 4, 8, 16, 22};
+
+static int pick_items(int m, int dtype)
 {
+    const int *c = dtype == TMFG_F32 ? kItemsF32 : kItemsF64;
+    const int nc = dtype == TMFG_F32 ? 8 : 6;
     for (int i = 0; i < nc; ++i)
-        if ((long long)choices[i] * kSortThreads >= m) return choices[i];
+        if ((long long)c[i] * kSortThreads >= m) return c[i];
     return -1;
 }
 
@@ -322,59 +368,88 @@ int64_t rowsort_max_n(int dtype)
     return m + 1;
 }
 
-#define TMFG_LAUNCH_SORT(KER, II)                                                              \
-    case II: {                                                                                 \
-        auto k = KER<II>;                                                                      \
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=      \
-            cudaSuccess)                                                                       \
-            return TMFG_ECUDA;                                                                 \
-        k<<<grid, kSortThreads, smem, stream>>>(reinterpret_cast<const ET *>(S), n, ld,        \
-                                                vec_in, idx, ldi, vec_out, rowsum, status);    \
-        break;                                                                                 \
+size_t rowsort_smem(int n, int dtype)
+{
+    return dtype == TMFG_F32 ? (size_t)sort_smem_f32(n - 1) : (size_t)sort_smem_f64(n - 1);
+}
+
+// Launch one kernel instance K<I, T> for the items count I (a switch over
+// the instantiated values).
+template <typename T, class F>
+static int dispatch_items(int I, F &&f)
+{
+    switch (I) {
+        case 1: return f(std::integral_constant<int, 1>{});
+        case 2: return f(std::integral_constant<int, 2>{});
+        case 4: return f(std::integral_constant<int, 4>{});
+        case 8: return f(std::integral_constant<int, 8>{});
+        case 16: return f(std::integral_constant<int, 16>{});
+        case 22:
+            if constexpr (sizeof(T) == 8) return f(std::integral_constant<int, 22>{});
+            return TMFG_EINTERNAL;
+        case 24:
+            if constexpr (sizeof(T) == 4) return f(std::integral_constant<int, 24>{});
+            return TMFG_EINTERNAL;
+        case 32:
+            if constexpr (sizeof(T) == 4) return f(std::integral_constant<int, 32>{});
+            return TMFG_EINTERNAL;
+        case 43:
+            if constexpr (sizeof(T) == 4) return f(std::integral_constant<int, 43>{});
+            return TMFG_EINTERNAL;
+        default: return TMFG_EINTERNAL;
     }
+}
+
+template <typename T>
+static int launch_rowsort_t(const void *S, int n, long long ld, uint16_t *idx, long long ldi,
+                            long long *rowsum, int *status, int num_sms, cudaStream_t stream)
+{
+    const int dtype = sizeof(T) == 4 ? TMFG_F32 : TMFG_F64;
+    const int I = pick_items(n - 1, dtype);
+    const size_t smem = rowsort_smem(n, dtype);
+    if (I < 0 || smem > (size_t)kSortSmemMax) return TMFG_ETOOBIG;
+    const bool vec_out = (ldi % 8 == 0) && ((uintptr_t)idx % 16 == 0);
+    const bool vec_in = (ld % (16 / sizeof(T)) == 0) && ((uintptr_t)S % 16 == 0);
+    const int grid = n < num_sms ? n : num_sms;
+    return dispatch_items<T>(I, [&](auto ic) {
+        constexpr int II = decltype(ic)::value;
+        auto k = rowsort_kernel<II, T>;
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return (int)TMFG_ECUDA;
+        k<<<grid, kSortThreads, smem, stream>>>(static_cast<const T *>(S), n, ld, vec_in, idx, ldi,
+                                                 vec_out, rowsum, status);
+        return cudaGetLastError() == cudaSuccess ? (int)TMFG_OK : (int)TMFG_ECUDA;
+    });
+}
 
 int launch_rowsort(const void *S, int n, long long ld, int dtype, uint16_t *idx, long long ldi,
                    long long *rowsum, int *status, int num_sms, cudaStream_t stream)
 {
-    const int m = n - 1;
-    const bool vec_out = (ldi % 8 == 0) && ((uintptr_t)idx % 16 == 0);
-    const int grid = n < num_sms ? n : num_sms;
-    if (dtype == TMFG_F32) {
-        using ET = float;
-        static const int choices[] = {1, 2, 4, 8, 16, 24, 32, 43};
-        const int I = pick_items(m, choices, 8);
-        const int smem = sort_smem_f32(m);
-        if (I < 0 || smem > kSortSmemMax) return TMFG_ETOOBIG;
-        const bool vec_in = (ld % 4 == 0) && ((uintptr_t)S % 16 == 0);
-        switch (I) {
-            TMFG_LAUNCH_SORT(rowsort_f32_kernel, 1)
-            TMFG_LAUNCH_SORT(rowsort_f32_kernel, 2)
-            TMFG_LAUNCH_SORT(rowsort_f32_kernel, 4)
-            TMFG_LAUNCH_SORT(rowsort_f32_kernel, 8)
-            TMFG_LAUNCH_SORT(rowsort_f32_kernel, 16)
-            TMFG_LAUNCH_SORT(rowsort_f32_kernel, 24)
-            TMFG_LAUNCH_SORT(rowsort_f32_kernel, 32)
-            TMFG_LAUNCH_SORT(rowsort_f32_kernel, 43)
-            default: return TMFG_EINTERNAL;
-        }
-    } else {
-        using ET = double;
-        static const int choices[] = {1, 2, 4, 8, 16, 22};
-        const int I = pick_items(m, choices, 6);
-        const int smem = sort_smem_f64(m);
-        if (I < 0 || smem > kSortSmemMax) return TMFG_ETOOBIG;
-        const bool vec_in = (ld % 2 == 0) && ((uintptr_t)S % 16 == 0);
-        switch (I) {
-            TMFG_LAUNCH_SORT(rowsort_f64_kernel, 1)
-            TMFG_LAUNCH_SORT(rowsort_f64_kernel, 2)
-            TMFG_LAUNCH_SORT(rowsort_f64_kernel, 4)
-            TMFG_LAUNCH_SORT(rowsort_f64_kernel, 8)
-            TMFG_LAUNCH_SORT(rowsort_f64_kernel, 16)
-            TMFG_LAUNCH_SORT(rowsort_f64_kernel, 22)
-            default: return TMFG_EINTERNAL;
-        }
-    }
-    return cudaGetLastError() == cudaSuccess ? TMFG_OK : TMFG_ECUDA;
+    if (dtype == TMFG_F32)
+        return launch_rowsort_t<float>(S, n, ld, idx, ldi, rowsum, status, num_sms, stream);
+    return launch_rowsort_t<double>(S, n, ld, idx, ldi, rowsum, status, num_sms, stream);
+}
+
+int launch_rowsort_batch(const SortJob *d_jobs, const int *d_row_begin, int njobs, int max_n,
+                         int dtype, int *status, int grid, cudaStream_t stream)
+{
+    const int I = pick_items(max_n - 1, dtype);
+    const size_t smem = rowsort_smem(max_n, dtype);
+    if (I < 0 || smem > (size_t)kSortSmemMax) return TMFG_ETOOBIG;
+    auto go = [&](auto tag) {
+        using T = decltype(tag);
+        return dispatch_items<T>(I, [&](auto ic) {
+            constexpr int II = decltype(ic)::value;
+            auto k = rowsort_batch_kernel<II, T>;
+            if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess)
+                return (int)TMFG_ECUDA;
+            k<<<grid, kSortThreads, smem, stream>>>(d_jobs, d_row_begin, njobs, status);
+            return cudaGetLastError() == cudaSuccess ? (int)TMFG_OK : (int)TMFG_ECUDA;
+        });
+    };
+    return dtype == TMFG_F32 ? go(float{}) : go(double{});
 }
 
 }  // namespace tmfg

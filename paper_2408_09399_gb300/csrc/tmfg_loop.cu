@@ -562,7 +562,7 @@ struct Loop {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kLoopThreads, 1) tmfg_loop_kernel(LoopArgs a)
+__device__ __forceinline__ void loop_body(const LoopArgs &a)
 {
     using KO = KeyOps<T>;
     using Key = typename KO::Key;
@@ -571,7 +571,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) tmfg_loop_kernel(LoopArgs a)
     __shared__ int s_n1[2], s_n2[2];
     __shared__ int s_vslow;
     __shared__ int s_nf, s_k, s_vcount, s_scan, s_evals, s_stop, s_nsel, s_fcount;
-    __shared__ int s_nx, s_ninv, s_nq1, s_nq2, s_np, s_more;
+    __shared__ int s_nx, s_ninv, s_nq1, s_np, s_more;
     __shared__ Key s_tau;
     __shared__ int s_clique[4];
     __shared__ long long s_red_r[kLoopWarps];
@@ -1042,15 +1042,17 @@ __global__ void __launch_bounds__(kLoopThreads, 1) tmfg_loop_kernel(LoopArgs a)
         for (int i = 0; i < 16; ++i) {
             acc[i] += seg[i];
             a.stats[i] = acc[i];
-            gscal[i] = acc[i];
+            if (gs) gscal[i] = acc[i];
         }
-        gscal[16] = s_nf;
-        gscal[17] = s_k;
-        Key *gr = reinterpret_cast<Key *>(gs + SL.off_roots);
-        gr[0] = s_root[0];
-        gr[1] = s_root[1];
+        if (gs) {
+            gscal[16] = s_nf;
+            gscal[17] = s_k;
+            Key *gr = reinterpret_cast<Key *>(gs + SL.off_roots);
+            gr[0] = s_root[0];
+            gr[1] = s_root[1];
+        }
     }
-    if (s_k < total && !s_stop) {
+    if (gs && s_k < total && !s_stop) {
         uint32_t *gins = reinterpret_cast<uint32_t *>(gs + SL.off_ins);
         uint16_t *gmc = reinterpret_cast<uint16_t *>(gs + SL.off_mc);
         uint16_t *gptr = reinterpret_cast<uint16_t *>(gs + SL.off_ptr);
@@ -1066,6 +1068,23 @@ __global__ void __launch_bounds__(kLoopThreads, 1) tmfg_loop_kernel(LoopArgs a)
         save_tree(st.tf, 0);
         if (heap) save_tree(st.ts, 1);
     }
+}
+
+// One instance per launch (the arguments by value).
+template <typename T>
+__global__ void __launch_bounds__(kLoopThreads, 1) tmfg_loop_kernel(LoopArgs a)
+{
+    loop_body<T>(a);
+}
+
+// Many instances per launch: CTA b runs instance b (arguments in global memory).
+template <typename T>
+__global__ void __launch_bounds__(kLoopThreads, 2) tmfg_loop_batch_kernel(const LoopArgs *args)
+{
+    __shared__ LoopArgs s_args;
+    if (threadIdx.x == 0) s_args = args[blockIdx.x];
+    __syncthreads();
+    loop_body<T>(s_args);
 }
 
 // Between loop segments: drop the inserted ids from every sorted row.  Row
@@ -1204,6 +1223,23 @@ int launch_loop(const LoopArgs &args, int dtype, cudaStream_t stream)
                                                              args.ldi, args.n, args.state,
                                                              args.status);
     }
+    return cudaGetLastError() == cudaSuccess ? TMFG_OK : TMFG_ECUDA;
+}
+
+int launch_loop_batch(const LoopArgs *d_args, int count, int max_n, int dtype, int mode,
+                      cudaStream_t stream)
+{
+    const size_t smem = loop_smem_bytes(max_n, dtype, mode);
+    if (smem > kSmemLimit || 2 * (size_t)max_n - 4 > 65535) return TMFG_ETOOBIG;
+    auto kf = tmfg_loop_batch_kernel<float>;
+    auto kd = tmfg_loop_batch_kernel<double>;
+    if (cudaFuncSetAttribute(dtype == TMFG_F32 ? (const void *)kf : (const void *)kd,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return TMFG_ECUDA;
+    if (dtype == TMFG_F32)
+        kf<<<count, kLoopThreads, smem, stream>>>(d_args);
+    else
+        kd<<<count, kLoopThreads, smem, stream>>>(d_args);
     return cudaGetLastError() == cudaSuccess ? TMFG_OK : TMFG_ECUDA;
 }
 

@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--n", type=int, default=20000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-requests", type=int, default=512)
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -288,12 +290,108 @@ def run_ours(args, rank, world, local):
         "e2e": e2e,
         "gpu_launches": KERNELS_PER_STEP * args.steps,
     }
+    if not args.no_batch:
+        result["batched"] = run_batched(T, ctx, args.batch_requests, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(S.cpu().numpy(), n)
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return result
+
+
+def run_batched(T, ctx, nreq, stream):
+    """Many small clustering instances (the serving request shape: n
+    log-uniform in [64, 4000], T in [128, 2048], 2-30 planted clusters):
+    TMFG (corr-tmfg P=1) + exact APSP per request, one instance per launch
+    sequence versus tmfg_batch_run, plain and replayed from a CUDA graph."""
+    import torch
+    from paper_2408_09399_gb300 import autotune
+    from paper_2408_09399_gb300 import workloads as W
+    reqs = W.serving_requests(1005, nreq, device=f"cuda:{torch.cuda.current_device()}")
+    mats = [r["S"] for r in reqs]
+    dev = mats[0].device
+
+    def alloc():
+        outs = []
+        for S in mats:
+            n = S.shape[0]
+            outs.append({"order": torch.empty(n, dtype=torch.int32, device=dev),
+                         "edges": torch.empty((3 * n - 6, 2), dtype=torch.int32, device=dev),
+                         "ins_face": torch.empty((n - 4, 3), dtype=torch.int32, device=dev),
+                         "bubble_parent": torch.empty(n - 3, dtype=torch.int32, device=dev),
+                         "D": torch.empty((n, n), dtype=torch.float32, device=dev)})
+        return outs
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    # plain: one instance per launch sequence, in arrival order
+    plain = alloc()
+    for S, o in zip(mats[:4], plain[:4]):
+        T.tmfg_build(ctx, S, MODE, 1, out=o, stream=stream)
+        T.tmfg_apsp(ctx, S, o["edges"], D=o["D"], stream=stream)
+    T.tmfg_sync_status(ctx, stream)
+    marks = [ev() for _ in range(nreq + 1)]
+    marks[0].record(stream)
+    for i, (S, o) in enumerate(zip(mats, plain)):
+        T.tmfg_build(ctx, S, MODE, 1, out=o, stream=stream)
+        T.tmfg_apsp(ctx, S, o["edges"], D=o["D"], stream=stream)
+        marks[i + 1].record(stream)
+    T.tmfg_sync_status(ctx, stream)
+    lat = [marks[i].elapsed_time(marks[i + 1]) for i in range(nreq)]
+    plain_ms = marks[0].elapsed_time(marks[-1])
+    # batched, launch shapes from the autotuner
+    cfg = autotune.tune_batch(ctx, mats[: min(nreq, 128)], MODE, 1, repeats=2)
+    batched = alloc()
+    chunk = cfg["chunk"]
+
+    def run_all():
+        for i in range(0, nreq, chunk):
+            T.tmfg_batch_run(ctx, mats[i:i + chunk], MODE, 1, apsp=True,
+                             sssp_threads=cfg["sssp_threads"], outs=batched[i:i + chunk],
+                             stream=stream)
+
+    run_all()
+    T.tmfg_sync_status(ctx, stream)
+    a, b = ev(), ev()
+    a.record(stream)
+    run_all()
+    b.record(stream)
+    T.tmfg_sync_status(ctx, stream)
+    batch_ms = a.elapsed_time(b)
+    same = all(torch.equal(x["edges"], y["edges"]) and torch.equal(x["D"], y["D"])
+               for x, y in zip(plain, batched))
+    # the batched run replayed from a captured CUDA graph (one launch per
+    # chunk, so the graph needs a single chunk to replay unchanged)
+    graph_ms = None
+    if chunk >= nreq:
+        g = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream()
+        cs.wait_stream(stream)
+        with torch.cuda.graph(g, stream=cs):
+            T.tmfg_batch_run(ctx, mats, MODE, 1, apsp=True, sssp_threads=cfg["sssp_threads"],
+                             outs=batched, stream=cs)
+        stream.wait_stream(cs)
+        g.replay()
+        T.tmfg_sync_status(ctx, stream)
+        a, b = ev(), ev()
+        a.record(stream)
+        g.replay()
+        b.record(stream)
+        T.tmfg_sync_status(ctx, stream)
+        graph_ms = a.elapsed_time(b)
+        same = same and all(torch.equal(x["edges"], y["edges"]) for x, y in zip(plain, batched))
+    lat_sorted = sorted(lat)
+    ns = [int(S.shape[0]) for S in mats]
+    return {"requests": nreq, "n_range": [min(ns), max(ns)], "n_mean": round(float(np.mean(ns)), 1),
+            "tmfg": "corr-tmfg P=1 + exact APSP",
+            "plain_solves_per_s": round(nreq / (plain_ms / 1e3), 1),
+            "plain_p50_ms": round(lat_sorted[len(lat) // 2], 3),
+            "plain_p99_ms": round(lat_sorted[min(len(lat) - 1, int(0.99 * len(lat)))], 3),
+            "batched_solves_per_s": round(nreq / (batch_ms / 1e3), 1),
+            "batched_ms": round(batch_ms, 3),
+            "graph_solves_per_s": round(nreq / (graph_ms / 1e3), 1) if graph_ms else None,
+            "speedup_vs_plain": round(plain_ms / batch_ms, 2),
+            "autotune": cfg, "outputs_identical": bool(same)}
 
 
 def cpu_baseline(Sn, n):

@@ -158,7 +158,12 @@ typedef struct {
  * each n must satisfy 4 <= n <= tmfg_max_n(dtype).  Asynchronous; the
  * descriptors are copied through the context's pinned staging buffer, so
  * the host array may be reused once the call returns.  The loop runs in one
- * segment per instance (no row compaction), which suits small instances. */
+ * segment per instance (no row compaction), which suits small instances.
+ * The call may be captured into a CUDA graph once the same batch has run
+ * uncaptured on the context (nothing is allocated or awaited under capture;
+ * TMFG_ENOMEM if it would have to); the captured descriptor copy reads the
+ * context's staging buffer at each replay, so a context that serves a
+ * captured graph must not run other batches in between. */
 int tmfg_batch_run(tmfg_ctx *ctx, const tmfg_job *jobs, int32_t count, const tmfg_params *params,
                    const tmfg_batch_config *cfg, void *stream);
 

@@ -340,11 +340,20 @@ int tmfg_batch_run(tmfg_ctx *ctx, const tmfg_job *jobs, int32_t count, const tmf
     }
     deg_bytes = round256(deg_bytes);
     const size_t total = tables + build_bytes + deg_bytes + apsp_bytes;
+    // Under stream capture nothing may allocate or wait: the workspace and
+    // the staging buffer must already be large enough (run the same batch
+    // once uncaptured first), and the captured descriptor copy reads the
+    // staging buffer when the graph is replayed.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return TMFG_ECUDA;
+    const bool capturing = cs != cudaStreamCaptureStatusNone;
+    if (capturing && (total > ctx->work_bytes || tables > ctx->stage_bytes)) return TMFG_ENOMEM;
     int rc = ensure_work(ctx, total, st);
     if (rc) return rc;
 
     // ---- host staging buffer (reused once its last copy has completed)
-    if (ctx->stage_used && cudaEventSynchronize(ctx->stage_ev) != cudaSuccess) return TMFG_ECUDA;
+    if (!capturing && ctx->stage_used && cudaEventSynchronize(ctx->stage_ev) != cudaSuccess)
+        return TMFG_ECUDA;
     if (ctx->stage_bytes < tables) {
         if (ctx->stage) cudaFreeHost(ctx->stage);
         ctx->stage = nullptr;
@@ -461,10 +470,12 @@ int tmfg_batch_run(tmfg_ctx *ctx, const tmfg_job *jobs, int32_t count, const tmf
     h_rows[count] = row_acc;
     h_ebeg[napsp] = edge_acc;
     h_sbeg[napsp] = src_acc;
-    if (cudaMemcpyAsync(db, hb, tables, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaEventRecord(ctx->stage_ev, st) != cudaSuccess)
+    if (cudaMemcpyAsync(db, hb, tables, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return TMFG_ECUDA;
-    ctx->stage_used = true;
+    if (!capturing) {
+        if (cudaEventRecord(ctx->stage_ev, st) != cudaSuccess) return TMFG_ECUDA;
+        ctx->stage_used = true;
+    }
     if (napsp && cudaMemsetAsync(deg, 0, deg_bytes, st) != cudaSuccess) return TMFG_ECUDA;
 
     rc = launch_rowsort_batch(d_sort, d_rows, count, max_n, dtype, ctx->status,

@@ -202,3 +202,35 @@ def random_similarity(seed: int, n: int, dtype=np.float32, kind: str = "uniform"
         flip = flip | flip.T
         S[z & flip] = -0.0
     return np.ascontiguousarray(S)
+
+
+def serving_requests(seed: int, count: int, device: str = "cuda", n_range=(64, 4000),
+                     T_range=(128, 2048), k_range=(2, 30), loading=(0.5, 0.9)):
+    """Clustering requests shaped like the serving workload: n log-uniform in
+    n_range, series length T uniform in T_range, planted cluster count k
+    uniform in k_range, strong loadings (clean instances).  The sizes come
+    from the counter-based generator above; the series themselves are drawn
+    with torch's generator seeded from (seed, request), on ``device``, which
+    keeps generation of thousands of requests fast (they are reproducible on
+    one device type, not across CPU and GPU).  Returns a list of dicts with
+    the float32 Pearson matrix S, the labels and the shape."""
+    import torch
+    u = uniform(seed, "req_n", count)
+    ns = np.round(np.exp(np.log(n_range[0]) + u * (np.log(n_range[1]) - np.log(n_range[0]))))
+    Ts = T_range[0] + (uniform(seed, "req_T", count) * (T_range[1] - T_range[0] + 1)).astype(int)
+    ks = k_range[0] + (uniform(seed, "req_k", count) * (k_range[1] - k_range[0] + 1)).astype(int)
+    out = []
+    for i in range(count):
+        n, T, k = int(ns[i]), int(Ts[i]), int(min(ks[i], ns[i] // 2))
+        g = torch.Generator(device=device)
+        g.manual_seed(int(u64(seed, "req_seed", 1, i)[0] >> np.uint64(1)))
+        lab = torch.randint(0, k, (n,), generator=g, device=device)
+        lam = loading[0] + (loading[1] - loading[0]) * torch.rand(n, generator=g, device=device)
+        F = torch.randn(k, T, generator=g, device=device)
+        X = lam[:, None] * F[lab] + torch.randn(n, T, generator=g, device=device)
+        X = X - X.mean(dim=1, keepdim=True)
+        X = X / torch.sqrt((X * X).sum(dim=1, keepdim=True))
+        S = X @ X.T
+        S.fill_diagonal_(1.0)
+        out.append({"S": S.contiguous(), "labels": lab, "n": n, "T": T, "k": k})
+    return out

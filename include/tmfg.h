@@ -71,7 +71,8 @@ void tmfg_destroy(tmfg_ctx *ctx);
 int64_t tmfg_max_n(int dtype);
 
 /* Workspace bytes that tmfg_build (what = 0), tmfg_apsp exact (what = 1)
- * or approximate (what = 2, with n_hubs = 0 meaning ceil(sqrt n)) needs. */
+ * or approximate (what = 2, with n_hubs = 0 meaning ceil(sqrt n)), or
+ * dbht_cluster (what = 3) needs. */
 size_t tmfg_workspace_bytes(int64_t n, int dtype, int what, int n_hubs);
 
 typedef struct {
@@ -166,6 +167,65 @@ typedef struct {
  * captured graph must not run other batches in between. */
 int tmfg_batch_run(tmfg_ctx *ctx, const tmfg_job *jobs, int32_t count, const tmfg_params *params,
                    const tmfg_batch_config *cfg, void *stream);
+
+/* Largest n accepted by dbht_cluster (its bubble-tree pass keeps 10 bytes
+ * per bubble in one CTA's shared memory). */
+#define DBHT_MAX_N 23247
+
+/* Optional per-vertex and per-bubble results of dbht_cluster_detail (device
+ * pointers, each may be NULL). */
+typedef struct {
+    int32_t *direction;  /* [n-4] bubble-tree edge k = 1..n-4 (entry k-1):
+                            1 = points from parent(k) into bubble k's side */
+    int32_t *converging; /* [n-3] 1 = bubble has no outgoing edge */
+    int32_t *group;      /* [n] converging bubble of each vertex */
+    int32_t *bubble;     /* [n] bubble of each vertex */
+} dbht_outputs;
+
+/* DBHT dendrogram (Section 2, "PMFG, TMFG, and DBHT": directed bubble tree,
+ * converging bubbles, vertex assignment, complete linkage inside bubbles,
+ * then within groups, then across groups) from a TMFG written by tmfg_build
+ * and its distances written by tmfg_apsp.  The paper sketches DBHT without
+ * fixing its rules; the reading implemented (identically by the test
+ * oracle) is:
+ *  - bubble 0 = the initial clique order[0..3]; bubble k >= 1 = {order[k+3]}
+ *    plus the face ins_face[k-1]; the bubble-tree edge (bubble_parent[k], k)
+ *    crosses that face t_k;
+ *  - edge k points toward bubble k's side iff the sum of q(S[a,b]) over the
+ *    TMFG edges (a,b) with a in t_k and b inside exceeds the sum over those
+ *    with b outside, where inside = vertices introduced by bubbles of k's
+ *    subtree and q(x) = x*2^40 rounded to the nearest integer, ties to even
+ *    (exact int64 sums); otherwise (ties too) it points to the parent;
+ *  - converging bubbles have no outgoing edge.  A vertex's group is the
+ *    converging bubble of least mean D to its 4 vertices; a non-converging
+ *    bubble's home is the converging bubble of least mean D over the 16
+ *    vertex pairs; a vertex's bubble is the bubble of least mean D to its
+ *    4 vertices among those whose home is the vertex's group.  Means are
+ *    double sums in vertex order divided by 4 or 16; ties to the smaller
+ *    bubble id;
+ *  - complete linkage over D inside each (group, bubble) cell (bubbles in
+ *    id order), then over the cells of each group (groups in converging
+ *    bubble order), then over the groups; each merge takes the pair of least
+ *    complete-linkage distance, ties to the pair whose (smaller, larger)
+ *    least leaf ids are lexicographically smallest.
+ * D is read as D[min(i,j)*ldd + max(i,j)] and must hold non-negative,
+ * non-NaN floats (as tmfg_apsp writes them).  linkage: (n-1) x 4 doubles in
+ * the scipy layout (id_lo, id_hi, height, size; leaves 0..n-1, merge r
+ * creates cluster n + r).  Order/edges/face/parent indices are checked on
+ * the device (TMFG_EINVAL in the status word if out of range or if order is
+ * not a permutation).  Workspace: tmfg_workspace_bytes(n, dtype, 3, 0)
+ * (about 4 n^2 bytes).  TMFG_ETOOBIG for n > DBHT_MAX_N. */
+int dbht_cluster(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, int32_t dtype,
+                 const int32_t *order, const int32_t *edges, const int32_t *ins_face,
+                 const int32_t *bubble_parent, const float *D, int64_t ldd, double *linkage,
+                 void *stream);
+
+/* dbht_cluster that also writes the intermediate results named in `out`
+ * (NULL: none). */
+int dbht_cluster_detail(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, int32_t dtype,
+                        const int32_t *order, const int32_t *edges, const int32_t *ins_face,
+                        const int32_t *bubble_parent, const float *D, int64_t ldd,
+                        double *linkage, const dbht_outputs *out, void *stream);
 
 /* Largest n accepted by tmfg_apsp_exact_noalloc. */
 #define TMFG_NOALLOC_MAX_N 21581

@@ -50,6 +50,11 @@ class _BatchConfig(ctypes.Structure):
     _fields_ = [("sssp_threads", ctypes.c_int32)]
 
 
+class _DbhtOutputs(ctypes.Structure):
+    _fields_ = [("direction", ctypes.c_void_p), ("converging", ctypes.c_void_p),
+                ("group", ctypes.c_void_p), ("bubble", ctypes.c_void_p)]
+
+
 class _ApspParams(ctypes.Structure):
     _fields_ = [("approx", ctypes.c_int32), ("n_hubs", ctypes.c_int32),
                 ("radius_factor", ctypes.c_float)]
@@ -83,6 +88,11 @@ def load_library():
         lib.tmfg_batch_run.argtypes = [P, ctypes.POINTER(_Job), ctypes.c_int32,
                                        ctypes.POINTER(_Params), ctypes.POINTER(_BatchConfig), P]
         lib.tmfg_batch_run.restype = ctypes.c_int
+        lib.dbht_cluster.argtypes = [P, P, i64, i64, i32, P, P, P, P, P, i64, P, P]
+        lib.dbht_cluster.restype = ctypes.c_int
+        lib.dbht_cluster_detail.argtypes = [P, P, i64, i64, i32, P, P, P, P, P, i64, P,
+                                            ctypes.POINTER(_DbhtOutputs), P]
+        lib.dbht_cluster_detail.restype = ctypes.c_int
         lib.tmfg_sync_status.argtypes = [P, P]
         lib.tmfg_sync_status.restype = ctypes.c_int
         lib.tmfg_last_stats.argtypes = [P, P, ctypes.c_int]
@@ -239,6 +249,56 @@ def tmfg_apsp(ctx: Context, S, edges, approx: bool = False, n_hubs: int = 0,
                                   _dev_ptr(D, torch.float32), D.stride(0), _stream_handle(stream))
     _check(rc, "tmfg_apsp")
     return D
+
+
+def _dbht_args(ctx, S, t, D):
+    torch = _torch()
+    n = S.shape[0]
+    dt = _mat_dtype(S)
+    if D.dtype != torch.float32 or D.dim() != 2 or D.stride(1) != 1:
+        raise TypeError("D must be a row-major float32 matrix")
+    i32 = torch.int32
+    return [ctx.handle, _dev_ptr(S), n, S.stride(0), dt,
+            _dev_ptr(t["order"], i32), _dev_ptr(t["edges"].contiguous(), i32),
+            _dev_ptr(t["ins_face"].contiguous(), i32) if n > 4 else None,
+            _dev_ptr(t["bubble_parent"], i32), _dev_ptr(D, torch.float32), D.stride(0)]
+
+
+def dbht_cluster(ctx: Context, S, t, D, linkage=None, stream=None):
+    """DBHT dendrogram of the TMFG ``t`` (the dict tmfg_build returns) with
+    distances D (float32, n x n).  Returns the (n-1) x 4 float64 linkage
+    (scipy layout) as a CUDA tensor."""
+    torch = _torch()
+    n = S.shape[0]
+    if linkage is None:
+        linkage = torch.empty((n - 1, 4), dtype=torch.float64, device=S.device)
+    rc = load_library().dbht_cluster(*_dbht_args(ctx, S, t, D),
+                                     _dev_ptr(linkage, torch.float64), _stream_handle(stream))
+    _check(rc, "dbht_cluster")
+    return linkage
+
+
+def dbht_cluster_detail(ctx: Context, S, t, D, linkage=None, stream=None):
+    """dbht_cluster that also returns the bubble-edge directions (n-4), the
+    converging-bubble flags (n-3), each vertex's group (converging bubble)
+    and bubble (n each), as int32 CUDA tensors.  Returns (linkage, info)."""
+    torch = _torch()
+    n = S.shape[0]
+    dev = S.device
+    if linkage is None:
+        linkage = torch.empty((n - 1, 4), dtype=torch.float64, device=dev)
+    info = {"direction": torch.zeros(max(n - 4, 1), dtype=torch.int32, device=dev),
+            "converging": torch.empty(n - 3, dtype=torch.int32, device=dev),
+            "group": torch.empty(n, dtype=torch.int32, device=dev),
+            "bubble": torch.empty(n, dtype=torch.int32, device=dev)}
+    outs = _DbhtOutputs(*[info[k].data_ptr() for k in ("direction", "converging", "group",
+                                                        "bubble")])
+    rc = load_library().dbht_cluster_detail(*_dbht_args(ctx, S, t, D),
+                                            _dev_ptr(linkage, torch.float64), ctypes.byref(outs),
+                                            _stream_handle(stream))
+    _check(rc, "dbht_cluster_detail")
+    info["direction"] = info["direction"][: max(n - 4, 0)]
+    return linkage, info
 
 
 def tmfg_batch_run(ctx: Context, mats, mode: str = "corr", prefix: int = 1, apsp: bool = True,

@@ -224,6 +224,7 @@ size_t tmfg_workspace_bytes(int64_t n, int dtype, int what, int n_hubs)
     (void)dtype;
     if (n < 4) return 0;
     if (what == 0) return build_work_bytes(n);
+    if (what == 3) return dbht_work_bytes((int)n);
     return apsp_work_bytes((int)n, what == 2, hubs_for(n, n_hubs));
 }
 
@@ -507,6 +508,37 @@ int tmfg_apsp(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, int32_t dtype
     if (rc) return rc;
     return launch_apsp(S, (int)n, ld, dtype, edges, approx, h, rf, D, ldd, ctx->work, ctx->status,
                        ctx->num_sms, ctx->timeout_ns, st);
+}
+
+int dbht_cluster_detail(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, int32_t dtype,
+                        const int32_t *order, const int32_t *edges, const int32_t *ins_face,
+                        const int32_t *bubble_parent, const float *D, int64_t ldd,
+                        double *linkage, const dbht_outputs *out, void *stream)
+{
+    if (!ctx || !S || !order || !edges || !bubble_parent || !D || !linkage || n < 4 || ld < n ||
+        ldd < n)
+        return TMFG_EINVAL;
+    if (n > 4 && !ins_face) return TMFG_EINVAL;
+    if (dtype != TMFG_F32 && dtype != TMFG_F64) return TMFG_EINVAL;
+    if (n > DBHT_MAX_N || dbht_smem_bytes((int)n) > kSmemLimit) return TMFG_ETOOBIG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return TMFG_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = ensure_work(ctx, dbht_work_bytes((int)n), st);
+    if (rc) return rc;
+    return launch_dbht(S, (int)n, ld, dtype, order, edges, ins_face, bubble_parent, D, ldd,
+                       linkage, out ? out->direction : nullptr, out ? out->converging : nullptr,
+                       out ? out->group : nullptr, out ? out->bubble : nullptr, ctx->work,
+                       ctx->status, ctx->num_sms, st);
+}
+
+int dbht_cluster(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, int32_t dtype,
+                 const int32_t *order, const int32_t *edges, const int32_t *ins_face,
+                 const int32_t *bubble_parent, const float *D, int64_t ldd, double *linkage,
+                 void *stream)
+{
+    return dbht_cluster_detail(ctx, S, n, ld, dtype, order, edges, ins_face, bubble_parent, D, ldd,
+                               linkage, nullptr, stream);
 }
 
 int tmfg_sync_status(tmfg_ctx *ctx, void *stream)

@@ -91,4 +91,12 @@ int launch_apsp(const void *S, int n, long long ld, int dtype, const int *edges,
 
 constexpr size_t kSmemLimit = 232448;  // 227 KB opt-in shared memory per CTA
 
+// dbht.cu
+size_t dbht_smem_bytes(int n);
+size_t dbht_work_bytes(int n);
+int launch_dbht(const void *S, int n, long long ld, int dtype, const int *order, const int *edges,
+                const int *ins_face, const int *parent, const float *D, long long ldd, double *Z,
+                int *direction, int *converging, int *group, int *bubble, void *work, int *status,
+                int num_sms, cudaStream_t stream);
+
 }  // namespace tmfg

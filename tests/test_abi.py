@@ -30,7 +30,7 @@ def lib():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("tmfg_create", "tmfg_destroy", "tmfg_build", "tmfg_apsp",
-                     "tmfg_sync_status", "tmfg_strerror", "tmfg_row_sort"):
+                     "tmfg_sync_status", "tmfg_strerror", "tmfg_row_sort", "dbht_cluster"):
         assert required in names
 
 
@@ -50,6 +50,8 @@ def test_host_only_calls(lib):
     n = 20000
     assert lib.tmfg_workspace_bytes(n, 0, 0, 0) >= 2 * n * (n - 1)
     assert lib.tmfg_workspace_bytes(n, 0, 2, 0) > lib.tmfg_workspace_bytes(n, 0, 1, 0)
+    # DBHT: the three levels' distance matrices dominate (n^2 floats)
+    assert lib.tmfg_workspace_bytes(n, 0, 3, 0) >= 4 * n * n
     lib.tmfg_strerror.restype = ctypes.c_char_p
     assert lib.tmfg_strerror(0) == b"ok"
     assert b"symmetric" in lib.tmfg_strerror(4)
@@ -61,6 +63,10 @@ def test_argument_errors_need_no_device(lib):
     assert lib.tmfg_build(None, None, 3, 3, None, None, None, None, None, None) == 1
     lib.tmfg_sync_status.argtypes = [P, P]
     assert lib.tmfg_sync_status(None, None) == 1
+    i64 = ctypes.c_int64
+    lib.dbht_cluster.argtypes = [P, P, i64, i64, ctypes.c_int32, P, P, P, P, P, i64, P, P]
+    assert lib.dbht_cluster(None, None, 10, 10, 0, None, None, None, None, None, 10, None,
+                            None) == 1
 
 
 def test_package_fails_loudly_without_a_device():

@@ -35,7 +35,46 @@ METRIC = "TMFG+APSP ms at n=20k"
 # corr-tmfg (Algorithm 1) with prefix 1 is the timed TMFG; heap-tmfg
 # (Algorithm 2) and corr-tmfg with prefix 10 are timed beside it
 MODE = "corr"
-KERNELS_PER_STEP = 14  # rowsort, loop; 4 exact-APSP kernels; 8 approximate-APSP kernels
+
+
+def kernels_per_step(n):
+    """Our kernel launches in one step: the row sort; the insertion loop in 6
+    segments with 5 row compactions between them (1 segment below n = 1024);
+    4 exact-APSP kernels (3 CSR + search); 8 approximate-APSP kernels (3 CSR,
+    hub pick, hub searches, nearest hub, bounded searches, symmetric min)."""
+    seg = 6 if n >= 1024 else 1
+    return 1 + seg + (seg - 1) + 4 + 8
+
+
+def cut_labels(Z, n, k):
+    """Clusters left after the first n-k merges of a linkage (union-find)."""
+    parent = np.arange(2 * n - 1)
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+
+    for r in range(n - k):
+        parent[find(int(Z[r, 0]))] = n + r
+        parent[find(int(Z[r, 1]))] = n + r
+    roots = np.array([find(v) for v in range(n)])
+    return np.unique(roots, return_inverse=True)[1]
+
+
+def adjusted_rand(a, b):
+    """Adjusted Rand index of two labelings (Hubert & Arabie), from the
+    contingency table."""
+    a = np.unique(a, return_inverse=True)[1]
+    b = np.unique(b, return_inverse=True)[1]
+    c = np.zeros((a.max() + 1, b.max() + 1), np.int64)
+    np.add.at(c, (a, b), 1)
+    comb = lambda x: x * (x - 1) / 2.0  # noqa: E731
+    sc, sa, sb = comb(c).sum(), comb(c.sum(1)).sum(), comb(c.sum(0)).sum()
+    exp = sa * sb / comb(len(a))
+    den = 0.5 * (sa + sb) - exp
+    return 1.0 if den == 0 else float((sc - exp) / den)
 
 
 def parse():
@@ -117,8 +156,7 @@ class ClockSampler:
 
 def make_input(n, device):
     from paper_2408_09399_gb300 import workloads as W
-    S, _ = W.config_similarity(3, device=device, n=n)
-    return S
+    return W.config_similarity(3, device=device, n=n)
 
 
 def measured_peaks():
@@ -142,7 +180,7 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     n = args.n
-    S = make_input(n, f"cuda:{local}")
+    S, labels = make_input(n, f"cuda:{local}")
     ctx = T.tmfg_create(local)
     stream = torch.cuda.current_stream()
     out = {"order": torch.empty(n, dtype=torch.int32, device=dev),
@@ -211,6 +249,25 @@ def run_ours(args, rank, world, local):
     T.tmfg_sync_status(ctx, stream)
     sort_ms = float(np.mean([a.elapsed_time(b) for a, b in sort_times]))
 
+    # DBHT dendrogram of the step's TMFG and exact distances (after the
+    # timed step, not part of it), and the ARI of its cut at the planted k
+    Z = torch.empty((n - 1, 4), dtype=torch.float64, device=dev)
+    T.dbht_cluster(ctx, S, out, D, linkage=Z, stream=stream)
+    T.tmfg_sync_status(ctx, stream)
+    dbht_times = []
+    for _ in range(3):
+        a, b = ev(), ev()
+        a.record(stream)
+        T.dbht_cluster(ctx, S, out, D, linkage=Z, stream=stream)
+        b.record(stream)
+        dbht_times.append((a, b))
+    T.tmfg_sync_status(ctx, stream)
+    k_true = len(np.unique(labels))
+    dbht = {"dbht_ms": round(float(np.mean([a.elapsed_time(b) for a, b in dbht_times])), 3),
+            "ari_at_planted_k": round(adjusted_rand(labels, cut_labels(Z.cpu().numpy(), n,
+                                                                       k_true)), 4),
+            "planted_k": int(k_true)}
+
     # the other TMFG variants on the same input (not part of the timed step)
     alt = {}
     for name, (mode, P) in {"heap_p1": ("heap", 1), "corr_p10": ("corr", 10)}.items():
@@ -222,21 +279,39 @@ def run_ours(args, rank, world, local):
         alt[name] = {"tmfg_ms": round(a.elapsed_time(b), 3),
                      "loop_ms": round(T.tmfg_last_stats(ctx)["loop_ns"] / 1e6, 3)}
 
-    # roofline of the dominant HBM-bound kernel and of the whole step
+    # Roofline.  The dominant kernel is the insertion loop (about 87 % of the
+    # step): a chain of n-4 dependent insertions, each a few dependent global
+    # memory round trips, so it sits far below every roof.  Its algorithmic
+    # bytes are the sector-granular gathers it must make: 9 S entries (one
+    # 32-byte sector each) per face evaluation plus 32 bytes per sorted-row
+    # probe.  The row sort and the two APSPs are listed beside it with their
+    # own algorithmic bytes (sort: read S 4n^2 + write ids 2n^2; APSP: write
+    # D 4n^2).
     hbm_peak, peak_kind = measured_peaks()
     phases = {"sort_rowsum_ms": sort_ms, "loop_ms": loop_ms, "tmfg_total_ms": tmfg_ms,
               "apsp_exact_ms": apsp_ms, "apsp_approx_ms": apsx_ms}
-    # algorithmic bytes: sort reads S (4n^2) and writes the index rows (2n^2);
-    # each APSP writes D (4n^2)
-    alg = {"sort": 6.0 * n * n, "apsp_exact": 4.0 * n * n, "apsp_approx": 4.0 * n * n}
-    cand = {"sort": sort_ms, "apsp_exact": apsp_ms, "apsp_approx": apsx_ms}
-    dom = max(cand, key=cand.get)
-    achieved = alg[dom] / (cand[dom] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm_peak,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
-                "traffic": None,
-                "note": "the heap insertion loop (loop_ms) is a chain of n-4 dependent steps "
-                        "bound by memory latency, not bandwidth; it is reported as ns/step"}
+    loop_bytes = 288.0 * stats["face_evals"] + 32.0 * stats["scan_chunks"]
+    # event-timed: the build (events around tmfg_build) minus the event-timed
+    # row sort leaves the loop segments and the row compactions between them
+    loop_ev_ms = max(tmfg_ms - sort_ms, 1e-6)
+    loop_gbs = loop_bytes / (loop_ev_ms * 1e-3) / 1e9
+
+    def line(bytes_, ms):
+        gbs = bytes_ / (ms * 1e-3) / 1e9
+        return {"achieved": round(gbs, 1), "frac": round(gbs / hbm_peak, 4),
+                "algorithmic_bytes": int(bytes_), "ms": round(ms, 3)}
+
+    roofline = {"bound": "hbm",
+                "kernel": "tmfg_loop_kernel (the 6 segments of one build, with the 5 row "
+                          "compactions between them)",
+                "achieved": round(loop_gbs, 2), "peak": hbm_peak, "peak_kind": peak_kind,
+                "unit": "GB/s", "frac": round(loop_gbs / hbm_peak, 5), "traffic": None,
+                "algorithmic_bytes": int(loop_bytes), "ms": round(loop_ev_ms, 3),
+                "note": "dependent-latency chain of n-4 insertions (ns per insertion in "
+                        "loop_ns_per_insertion); no roof binds it",
+                "other_kernels": {"rowsort": line(6.0 * n * n, sort_ms),
+                                  "apsp_exact": line(4.0 * n * n, apsp_ms),
+                                  "apsp_approx": line(4.0 * n * n, apsx_ms)}}
 
     e2e = None
     if not args.no_e2e and rank == 0:
@@ -283,12 +358,13 @@ def run_ours(args, rank, world, local):
         "loop_ns_per_insertion": round(stats["loop_ns"] / max(1, n - 4), 1),
         "loop_stats": stats,
         "tmfg_variants": alt,
+        "dbht": dbht,
         "roofline": roofline,
         "algorithmic_bytes_per_step": int(14 * n * n),
         "step_hbm_frac": round(14.0 * n * n / (ms_step * 1e-3) / 1e9 / hbm_peak, 4),
         "clocks": clk.summary(),
         "e2e": e2e,
-        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "gpu_launches": kernels_per_step(n) * args.steps,
     }
     if not args.no_batch:
         result["batched"] = run_batched(T, ctx, args.batch_requests, stream)
@@ -438,7 +514,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     n = args.n
-    Sn = make_input(n, "cpu")
+    Sn = make_input(n, "cpu")[0]
     vals = []
     last = None
     for i in range(args.warmup + args.steps):

@@ -17,12 +17,19 @@
 // recomputes the marked groups (a warp per group) and the root.
 //
 // MaxCorrs[w] is read fresh: the cached Mc[w] is kept while uninserted, else
-// one warp scans row w from ptr[w]+1 with 16-byte loads (256 sorted ids per
-// step) and a ballot over the inserted bitmap -- the lazily advanced pointer
-// of Section 4.3.  A face's best vertex is computed by one warp: 9 lanes
-// gather S[x,u] (3 candidates u x 3 face vertices x), gain = (S[a,u] +
-// S[b,u]) + S[c,u] with round-to-nearest adds in the dtype of S, ties to the
-// smaller u.
+// the lazily advanced pointer of Section 4.3 moves on -- first one thread
+// probes the next 16 sorted ids (two 16-byte reads) against the inserted
+// bitmap, and only rows whose probe finds nothing go to a warp that scans
+// 256 sorted ids per step with 16-byte loads and a ballot.  A face's best
+// vertex is computed by one thread: 9 independent gathers S[x,u] (3
+// candidates u x 3 face vertices x), gain = (S[a,u] + S[b,u]) + S[c,u] with
+// round-to-nearest adds in the dtype of S, ties to the smaller u.
+//
+// Segments.  The loop runs as a few launches (ending after 1/2, 3/4, ...,
+// 31/32 of the insertions); between them every sorted row is compacted to
+// its uninserted ids, so the pointers of late insertions do not wade through
+// long runs of inserted ids.  The loop state is saved to global memory at
+// the end of a segment and restored at the start of the next.
 //
 // corr-tmfg: one index over all faces.  A round takes the P best pairs
 // (repeated extraction), keeps the first pair of each vertex, inserts in

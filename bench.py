@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-requests", type=int, default=512)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2048)
+    ap.add_argument("--no-serve", action="store_true")
     return ap.parse_args()
 
 
@@ -368,6 +370,8 @@ def run_ours(args, rank, world, local):
     }
     if not args.no_batch:
         result["batched"] = run_batched(T, ctx, args.batch_requests, stream)
+    if not args.no_serve:
+        result["serving"] = run_serving(T, ctx, args.serve_requests, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(S.cpu().numpy(), n)
     ctx.close()
@@ -468,6 +472,133 @@ def run_batched(T, ctx, nreq, stream):
             "graph_solves_per_s": round(nreq / (graph_ms / 1e3), 1) if graph_ms else None,
             "speedup_vs_plain": round(plain_ms / batch_ms, 2),
             "autotune": cfg, "outputs_identical": bool(same)}
+
+
+def poisson_arrivals(seed, count, rate):
+    """Arrival offsets (s) of a Poisson process of `rate` per second, from the
+    counter-based generator (exponential gaps by inversion)."""
+    from paper_2408_09399_gb300 import workloads as W
+    u = W.uniform(seed, "arrivals", count)
+    return np.cumsum(-np.log(1.0 - u) / rate)
+
+
+def pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(q * len(xs)))]
+
+
+def run_serving(T, ctx, nreq, stream, lanes=3):
+    """Served clustering requests (TMFG corr P=1 + exact APSP each; n
+    log-uniform in [64, 4000], T in [128, 2048], 2-30 planted clusters)
+    arriving by a Poisson process at 0.8x and 1.5x the plain path's measured
+    capacity, through the continuous-batching server and through the plain
+    one-instance path under the same arrival times; then every request at
+    once.  Latency = completion seen by the host - arrival."""
+    import torch
+    from paper_2408_09399_gb300 import workloads as W
+    dev = torch.device("cuda", torch.cuda.current_device())
+    reqs = W.serving_requests(2005, nreq, device=str(dev))
+    mats = [r["S"] for r in reqs]
+    torch.cuda.synchronize()
+
+    def outputs(S):
+        n = S.shape[0]
+        return {"order": torch.empty(n, dtype=torch.int32, device=dev),
+                "edges": torch.empty((3 * n - 6, 2), dtype=torch.int32, device=dev),
+                "ins_face": torch.empty((n - 4, 3), dtype=torch.int32, device=dev),
+                "bubble_parent": torch.empty(n - 3, dtype=torch.int32, device=dev),
+                "D": torch.empty((n, n), dtype=torch.float32, device=dev)}
+
+    served_out = [outputs(S) for S in mats]
+    nmax = max(int(S.shape[0]) for S in mats)
+    scratch = outputs(torch.empty((nmax, nmax), device=dev))
+    now = T.tmfg_serve_now_ns
+
+    def plain_one(S, o):
+        n = S.shape[0]
+        oo = o if o is not None else {
+            "order": scratch["order"][:n], "edges": scratch["edges"][: 3 * n - 6],
+            "ins_face": scratch["ins_face"][: n - 4], "bubble_parent": scratch["bubble_parent"][: n - 3]}
+        D = o["D"] if o is not None else scratch["D"].view(-1)[: n * n].view(n, n)
+        T.tmfg_build(ctx, S, MODE, 1, out=oo, stream=stream)
+        T.tmfg_apsp(ctx, S, oo["edges"], D=D, stream=stream)
+        T.tmfg_sync_status(ctx, stream)
+
+    # plain capacity on the first requests (service time alone, no queueing)
+    k_cap = min(nreq, 256)
+    for S in mats[:4]:
+        plain_one(S, None)
+    t0 = now()
+    for S in mats[:k_cap]:
+        plain_one(S, None)
+    cap = k_cap / ((now() - t0) / 1e9)
+
+    def wait_until(t_ns):
+        while True:
+            d = t_ns - now()
+            if d <= 0:
+                return
+            if d > 200_000:
+                time.sleep((d - 100_000) / 1e9)
+
+    def run_plain(arr_s):
+        base = now() + 2_000_000
+        lat = []
+        for i, S in enumerate(mats):
+            t_arr = base + int(arr_s[i] * 1e9)
+            wait_until(t_arr)
+            plain_one(S, None)
+            lat.append((now() - t_arr) / 1e6)
+        span = (now() - base) / 1e9
+        return {"solves_per_s": round(nreq / span, 1), "p50_ms": round(pct(lat, 0.5), 3),
+                "p99_ms": round(pct(lat, 0.99), 3)}
+
+    def run_served(arr_s):
+        srv = T.tmfg_serve_start(torch.cuda.current_device(), lanes=lanes, max_batch=256,
+                                 mode=MODE, prefix=1)
+        res = {}
+        base = now() + 2_000_000
+        for i, S in enumerate(mats):
+            if arr_s is not None:
+                t_arr = base + int(arr_s[i] * 1e9)
+                while now() < t_arr:
+                    for r in T.tmfg_serve_poll(srv, 1024, 0):
+                        res[r["id"]] = r
+                    d = t_arr - now()
+                    if d > 200_000:
+                        time.sleep(min(d - 100_000, 1_000_000) / 1e9)
+            T.tmfg_serve_submit(srv, S, out=served_out[i], stream=stream)
+        while len(res) < nreq:
+            for r in T.tmfg_serve_poll(srv, 1024, 10000):
+                res[r["id"]] = r
+        T.tmfg_serve_stop(srv)
+        rs = list(res.values())
+        lat = [(r["t_done_ns"] - r["t_submit_ns"]) / 1e6 for r in rs]
+        first = min(r["t_submit_ns"] for r in rs)
+        last = max(r["t_done_ns"] for r in rs)
+        ok = all(r["status"] == 0 for r in rs)
+        return {"solves_per_s": round(nreq / ((last - first) / 1e9), 1),
+                "p50_ms": round(pct(lat, 0.5), 3), "p99_ms": round(pct(lat, 0.99), 3),
+                "mean_batch": round(float(np.mean([r["batch_size"] for r in rs])), 1),
+                "batches": len({r["batch"] for r in rs}), "all_ok": ok}
+
+    rates = []
+    for load in (0.8, 1.5):
+        arr = poisson_arrivals(6000 + int(load * 10), nreq, load * cap)
+        rates.append({"load_vs_plain_capacity": load, "offered_per_s": round(load * cap, 1),
+                      "served": run_served(arr), "plain": run_plain(arr)})
+    sat = run_served(None)
+    # equal accuracy: the served outputs equal the plain path's, bit for bit
+    same = True
+    for i in range(0, nreq, max(1, nreq // 64)):
+        o = outputs(mats[i])
+        plain_one(mats[i], o)
+        same = same and all(torch.equal(o[k], served_out[i][k]) for k in o)
+    ns = [int(S.shape[0]) for S in mats]
+    return {"requests": nreq, "n_range": [min(ns), max(ns)], "n_mean": round(float(np.mean(ns)), 1),
+            "lanes": lanes, "tmfg": "corr-tmfg P=1 + exact APSP",
+            "plain_capacity_solves_per_s": round(cap, 1), "poisson": rates,
+            "saturation": sat, "outputs_identical_sampled": bool(same)}
 
 
 def cpu_baseline(Sn, n):

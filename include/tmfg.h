@@ -227,6 +227,72 @@ int dbht_cluster_detail(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, int
                         const int32_t *bubble_parent, const float *D, int64_t ldd,
                         double *linkage, const dbht_outputs *out, void *stream);
 
+/* ------------------------------------------------------------ serving
+ * A request server with continuous batching (no counterpart in the paper).
+ * Jobs (tmfg_job, buffers resident in device memory, caller-owned) are
+ * submitted one by one; a host worker thread groups the waiting jobs, first
+ * come first served, into batches that run through tmfg_batch_run on one of
+ * `lanes` lanes.  Each lane is a context with its own non-blocking stream and
+ * a workspace of lane_bytes allocated at start, so batches on different lanes
+ * overlap on the GPU and nothing is allocated while serving.  A batch takes
+ * as many queued jobs as fit its lane's memory (tmfg_serve_request_bytes
+ * each, plus the descriptor tables) and max_batch; a job that does not fit
+ * an empty lane is refused at submission.  Every job gets exactly the result
+ * tmfg_build (and tmfg_apsp, exact) give it alone, whatever it is batched
+ * with.  A data error in a batch is reported for every job of that batch. */
+typedef struct tmfg_server tmfg_server;
+
+typedef struct {
+    int32_t lanes;         /* concurrent batches; 0 = 3 (at most 16) */
+    int32_t max_batch;     /* jobs per batch; 0 = 256 (at most 4096) */
+    size_t lane_bytes;     /* workspace per lane; 0 = 4 GiB */
+    tmfg_params params;    /* TMFG parameters of every job */
+    int32_t apsp;          /* 1: also the exact APSP into each job's D */
+    int32_t sssp_threads;  /* as in tmfg_batch_config; 0 = default */
+} tmfg_serve_config;
+
+typedef struct {
+    int64_t id;            /* as returned by tmfg_serve_submit */
+    int32_t status;        /* TMFG_OK or the error of the job's batch */
+    int32_t batch;         /* sequence number of the batch that ran it */
+    int32_t batch_size;    /* jobs in that batch */
+    int32_t reserved;
+    int64_t t_submit_ns;   /* tmfg_serve_now_ns clock: submission, */
+    int64_t t_launch_ns;   /*   launch of its batch, */
+    int64_t t_done_ns;     /*   completion seen by the host */
+} tmfg_serve_result;
+
+/* Start a server on `device` (creates the lanes and the worker thread). */
+int tmfg_serve_start(tmfg_server **out, int device, const tmfg_serve_config *cfg);
+
+/* Queue one job; returns its id (>= 0) or minus an error code.  The job's
+ * inputs count as ready once `stream` (the submitter's cudaStream_t as
+ * void*, NULL = legacy default) reaches the point of this call.  The
+ * descriptor is copied; its buffers must stay valid until the job's result
+ * has been polled. */
+int64_t tmfg_serve_submit(tmfg_server *s, const tmfg_job *job, void *stream);
+
+/* Move up to `max` finished jobs' results into out[] (waiting up to wait_us
+ * microseconds for the first); returns the count, or minus an error code.
+ * A job's outputs are complete on the device when its result is returned. */
+int tmfg_serve_poll(tmfg_server *s, tmfg_serve_result *out, int32_t max, int32_t wait_us);
+
+/* Finish every submitted job, stop the worker and free the server.
+ * Results not yet polled are discarded. */
+int tmfg_serve_stop(tmfg_server *s);
+
+/* The server's clock (steady, nanoseconds). */
+int64_t tmfg_serve_now_ns(void);
+
+/* Workspace bytes one job of size n needs in a lane (its admission unit). */
+size_t tmfg_serve_request_bytes(int64_t n, int32_t apsp);
+
+/* The batching rule alone, for inspection: the batch (0, 1, ...) that each
+ * of `count` jobs of sizes n[] queued together would fall into when lanes
+ * take them in order.  TMFG_ENOMEM if a job cannot fit an empty lane. */
+int tmfg_serve_plan(const int64_t *n, int32_t count, int32_t apsp, int32_t max_batch,
+                    size_t lane_bytes, int32_t *batch_of);
+
 /* Largest n accepted by tmfg_apsp_exact_noalloc. */
 #define TMFG_NOALLOC_MAX_N 21581
 

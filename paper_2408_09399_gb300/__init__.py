@@ -55,6 +55,19 @@ class _DbhtOutputs(ctypes.Structure):
                 ("group", ctypes.c_void_p), ("bubble", ctypes.c_void_p)]
 
 
+class _ServeConfig(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("lane_bytes", ctypes.c_size_t), ("params", _Params),
+                ("apsp", ctypes.c_int32), ("sssp_threads", ctypes.c_int32)]
+
+
+class _ServeResult(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("batch_size", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("t_submit_ns", ctypes.c_int64), ("t_launch_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64)]
+
+
 class _ApspParams(ctypes.Structure):
     _fields_ = [("approx", ctypes.c_int32), ("n_hubs", ctypes.c_int32),
                 ("radius_factor", ctypes.c_float)]
@@ -93,6 +106,21 @@ def load_library():
         lib.dbht_cluster_detail.argtypes = [P, P, i64, i64, i32, P, P, P, P, P, i64, P,
                                             ctypes.POINTER(_DbhtOutputs), P]
         lib.dbht_cluster_detail.restype = ctypes.c_int
+        lib.tmfg_serve_start.argtypes = [ctypes.POINTER(P), ctypes.c_int,
+                                         ctypes.POINTER(_ServeConfig)]
+        lib.tmfg_serve_start.restype = ctypes.c_int
+        lib.tmfg_serve_submit.argtypes = [P, ctypes.POINTER(_Job), P]
+        lib.tmfg_serve_submit.restype = i64
+        lib.tmfg_serve_poll.argtypes = [P, ctypes.POINTER(_ServeResult), i32, i32]
+        lib.tmfg_serve_poll.restype = ctypes.c_int
+        lib.tmfg_serve_stop.argtypes = [P]
+        lib.tmfg_serve_stop.restype = ctypes.c_int
+        lib.tmfg_serve_now_ns.argtypes = []
+        lib.tmfg_serve_now_ns.restype = i64
+        lib.tmfg_serve_request_bytes.argtypes = [i64, i32]
+        lib.tmfg_serve_request_bytes.restype = ctypes.c_size_t
+        lib.tmfg_serve_plan.argtypes = [P, i32, i32, i32, ctypes.c_size_t, P]
+        lib.tmfg_serve_plan.restype = ctypes.c_int
         lib.tmfg_sync_status.argtypes = [P, P]
         lib.tmfg_sync_status.restype = ctypes.c_int
         lib.tmfg_last_stats.argtypes = [P, P, ctypes.c_int]
@@ -336,6 +364,116 @@ def tmfg_batch_run(ctx: Context, mats, mode: str = "corr", prefix: int = 1, apsp
                                        ctypes.byref(cfg), _stream_handle(stream))
     _check(rc, "tmfg_batch_run")
     return outs
+
+
+class Server:
+    """Owns a tmfg_server (continuous-batching request server) and keeps each
+    request's tensors alive until its result has been polled."""
+
+    def __init__(self, device, cfg):
+        lib = load_library()
+        _torch()
+        h = ctypes.c_void_p()
+        _check(lib.tmfg_serve_start(ctypes.byref(h), int(device), ctypes.byref(cfg)),
+               "tmfg_serve_start")
+        self.handle = h
+        self.device = device
+        self.apsp = bool(cfg.apsp)
+        self.live = {}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            rc = load_library().tmfg_serve_stop(self.handle)
+            self.handle = None
+            self.live.clear()
+            _check(rc, "tmfg_serve_stop")
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tmfg_serve_start(device: int = 0, lanes: int = 0, max_batch: int = 0, lane_bytes: int = 0,
+                     mode: str = "corr", prefix: int = 1, dtype: int = TMFG_F32,
+                     apsp: bool = True, sssp_threads: int = 0) -> Server:
+    """Start a request server (see tmfg_serve_start in include/tmfg.h)."""
+    cfg = _ServeConfig(int(lanes), int(max_batch), int(lane_bytes),
+                       _Params({"corr": TMFG_CORR, "heap": TMFG_HEAP}[mode], int(prefix),
+                               int(dtype), 0),
+                       1 if apsp else 0, int(sssp_threads))
+    return Server(device, cfg)
+
+
+def tmfg_serve_submit(server: Server, S, out=None, stream=None) -> int:
+    """Queue the TMFG (and exact APSP) of S; returns the request id.  The
+    outputs (dict as from tmfg_build, plus D when the server runs APSP) are
+    allocated here unless given, and come back with the result."""
+    torch = _torch()
+    n = S.shape[0]
+    _mat_dtype(S)
+    if out is None:
+        dev = S.device
+        out = {"order": torch.empty(n, dtype=torch.int32, device=dev),
+               "edges": torch.empty((max(3 * n - 6, 0), 2), dtype=torch.int32, device=dev),
+               "ins_face": torch.empty((max(n - 4, 0), 3), dtype=torch.int32, device=dev),
+               "bubble_parent": torch.empty(max(n - 3, 0), dtype=torch.int32, device=dev)}
+        if server.apsp:
+            out["D"] = torch.empty((n, n), dtype=torch.float32, device=dev)
+    D = out.get("D")
+    job = _Job(S.data_ptr(), n, S.stride(0), out["order"].data_ptr(), out["edges"].data_ptr(),
+               out["ins_face"].data_ptr() if n > 4 else None, out["bubble_parent"].data_ptr(),
+               D.data_ptr() if D is not None else None, D.stride(0) if D is not None else 0)
+    rid = load_library().tmfg_serve_submit(server.handle, ctypes.byref(job),
+                                           _stream_handle(stream))
+    if rid < 0:
+        raise TmfgError(int(-rid), "tmfg_serve_submit")
+    server.live[int(rid)] = (S, out)
+    return int(rid)
+
+
+def tmfg_serve_poll(server: Server, max_results: int = 1024, wait_us: int = 0) -> list:
+    """Finished requests: dicts with id, status, batch, batch_size, the three
+    timestamps (ns) and the request's outputs."""
+    buf = (_ServeResult * max(1, int(max_results)))()
+    c = load_library().tmfg_serve_poll(server.handle, buf, int(max_results), int(wait_us))
+    if c < 0:
+        raise TmfgError(int(-c), "tmfg_serve_poll")
+    res = []
+    for i in range(c):
+        r = buf[i]
+        S, out = server.live.pop(int(r.id))
+        res.append({"id": int(r.id), "status": int(r.status), "batch": int(r.batch),
+                    "batch_size": int(r.batch_size), "t_submit_ns": int(r.t_submit_ns),
+                    "t_launch_ns": int(r.t_launch_ns), "t_done_ns": int(r.t_done_ns),
+                    "S": S, "out": out})
+    return res
+
+
+def tmfg_serve_stop(server: Server):
+    server.close()
+
+
+def tmfg_serve_now_ns() -> int:
+    return int(load_library().tmfg_serve_now_ns())
+
+
+def tmfg_serve_request_bytes(n: int, apsp: bool = True) -> int:
+    return int(load_library().tmfg_serve_request_bytes(int(n), 1 if apsp else 0))
+
+
+def tmfg_serve_plan(ns, apsp: bool = True, max_batch: int = 256, lane_bytes: int = 4 << 30):
+    """Batch index of each queued request under the admission rule (host
+    only; no device needed)."""
+    import numpy as np
+    n = np.ascontiguousarray(ns, np.int64)
+    out = np.empty(len(n), np.int32)
+    rc = load_library().tmfg_serve_plan(n.ctypes.data_as(ctypes.c_void_p), len(n),
+                                        1 if apsp else 0, int(max_batch), int(lane_bytes),
+                                        out.ctypes.data_as(ctypes.c_void_p))
+    _check(rc, "tmfg_serve_plan")
+    return out
 
 
 def tmfg_sync_status(ctx: Context, stream=None, raise_on_error: bool = True) -> int:

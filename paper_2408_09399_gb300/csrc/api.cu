@@ -5,7 +5,7 @@
 #include <cstring>
 #include <new>
 
-#include "internal.cuh"
+#include "ctx.cuh"
 
 namespace tmfg {
 
@@ -40,40 +40,8 @@ __global__ void symmetry_kernel(const T *__restrict__ S, long long ld, int n, in
 
 using namespace tmfg;
 
-struct tmfg_ctx {
-    int device;
-    int num_sms;
-    size_t budget;
-    void *work;
-    size_t work_bytes;
-    int *status;        // device word
-    long long *stats;   // device [8]
-    long long host_stats[16];
-    unsigned long long timeout_ns;
-    void *stage;          // pinned host staging buffer for batch descriptor tables
-    size_t stage_bytes;
-    cudaEvent_t stage_ev; // recorded after the last copy out of the staging buffer
-    bool stage_used;
-};
 
-namespace {
-
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = false;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) return;
-        ok = (prev == dev) || cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard()
-    {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
-size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
+namespace tmfg {
 
 int ensure_work(tmfg_ctx *c, size_t bytes, cudaStream_t stream)
 {
@@ -94,7 +62,42 @@ int ensure_work(tmfg_ctx *c, size_t bytes, cudaStream_t stream)
     return TMFG_OK;
 }
 
-long long ldi_for(int64_t n) { return ((n - 1) + 7) / 8 * 8; }
+int ensure_stage(tmfg_ctx *c, size_t bytes)
+{
+    if (c->stage_bytes >= bytes) return TMFG_OK;
+    if (c->stage) cudaFreeHost(c->stage);
+    c->stage = nullptr;
+    c->stage_bytes = 0;
+    if (cudaHostAlloc(&c->stage, bytes, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return TMFG_ENOMEM;
+    }
+    c->stage_bytes = bytes;
+    return TMFG_OK;
+}
+
+size_t batch_table_bytes(int count, int napsp)
+{
+    return round256(sizeof(SortJob) * count) + round256(sizeof(int) * (count + 1)) +
+           round256(sizeof(LoopArgs) * count) + round256(sizeof(ApspJob) * (napsp + 1)) +
+           round256(sizeof(SsspArgs) * (napsp + 1)) + 2 * round256(sizeof(int) * (napsp + 1));
+}
+
+size_t batch_request_bytes(int64_t n, bool apsp)
+{
+    const size_t nf = 2 * (size_t)n - 4;
+    size_t b = round256(2 * (size_t)n * (size_t)ldi_for(n)) + round256(8 * (size_t)n) +
+               round256(16 * nf) * 4 + round256(8 * nf) + round256(4 * nf) + 256;
+    if (apsp)
+        b += round256(4 * (size_t)n) + round256(4 * ((size_t)n + 1)) + round256(4 * (size_t)n) +
+             round256(8 * 2 * (3 * (size_t)n - 6));
+    return b;
+}
+
+}  // namespace tmfg
+
+namespace {
+
 
 struct BuildWork {
     uint16_t *idx;
@@ -327,6 +330,7 @@ int tmfg_batch_run(tmfg_ctx *ctx, const tmfg_job *jobs, int32_t count, const tmf
     const size_t t_ebeg = round256(sizeof(int) * (napsp + 1));
     const size_t t_sbeg = round256(sizeof(int) * (napsp + 1));
     const size_t tables = t_sort + t_rows + t_loop + t_ajob + t_sarg + t_ebeg + t_sbeg;
+    if (tables != batch_table_bytes(count, napsp)) return TMFG_EINTERNAL;
     size_t build_bytes = 0, apsp_bytes = 0, deg_bytes = 0;
     for (int i = 0; i < count; ++i) {
         const int64_t n = jobs[i].n;
@@ -355,16 +359,8 @@ int tmfg_batch_run(tmfg_ctx *ctx, const tmfg_job *jobs, int32_t count, const tmf
     // ---- host staging buffer (reused once its last copy has completed)
     if (!capturing && ctx->stage_used && cudaEventSynchronize(ctx->stage_ev) != cudaSuccess)
         return TMFG_ECUDA;
-    if (ctx->stage_bytes < tables) {
-        if (ctx->stage) cudaFreeHost(ctx->stage);
-        ctx->stage = nullptr;
-        ctx->stage_bytes = 0;
-        if (cudaHostAlloc(&ctx->stage, tables, cudaHostAllocDefault) != cudaSuccess) {
-            cudaGetLastError();
-            return TMFG_ENOMEM;
-        }
-        ctx->stage_bytes = tables;
-    }
+    rc = ensure_stage(ctx, tables);
+    if (rc) return rc;
     char *hb = static_cast<char *>(ctx->stage);
     char *db = static_cast<char *>(ctx->work);
     SortJob *h_sort = reinterpret_cast<SortJob *>(hb);

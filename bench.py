@@ -100,6 +100,34 @@ def dist_env():
     return rank, world, local
 
 
+def init_dist(device):
+    """One process per GPU (NCCL); gloo when `device` is the CPU.  The
+    rendezvous comes from MASTER_ADDR / MASTER_PORT / RANK / WORLD_SIZE."""
+    import torch
+    import torch.distributed as dist
+    if device.type == "cuda":
+        dist.init_process_group("nccl", device_id=device)
+    else:
+        dist.init_process_group("gloo")
+    return dist
+
+
+def max_over_ranks(x, device):
+    """The largest of every rank's x (each rank gets it).  Ranks solve
+    independent instances, so this is the only exchange: the job's time."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_ms(ms_step, world):
+    """Whole-job time per solved instance: every rank solved one instance
+    in the (max-over-ranks) step time."""
+    return ms_step / world
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples while the timed region runs."""
 
@@ -179,8 +207,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+        init_dist(dev)
     n = args.n
     S, labels = make_input(n, f"cuda:{local}")
     ctx = T.tmfg_create(local)
@@ -226,11 +253,8 @@ def run_ours(args, rank, world, local):
     stats = T.tmfg_last_stats(ctx)
     total_ms = t0.elapsed_time(t1)
     if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-        dist.barrier()
+        total_ms = max_over_ranks(total_ms, dev)
+        torch.distributed.barrier()
     ms_step = total_ms / args.steps
     ph = np.array([[a.elapsed_time(b), b.elapsed_time(c), c.elapsed_time(d)]
                    for a, b, c, d in times])
@@ -347,7 +371,8 @@ def run_ours(args, rank, world, local):
                "d2h_bytes_per_step": 2 * 4 * n * n + 4 * 2 * (3 * n - 6)}
 
     result = {
-        "metric": METRIC, "value": round(ms_step, 3), "unit": "ms", "n_gpus": world,
+        "metric": METRIC, "value": round(whole_job_ms(ms_step, world), 3), "unit": "ms",
+        "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",

@@ -90,6 +90,10 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2048)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-sim", action="store_true")
+    ap.add_argument("--sim-only", action="store_true",
+                    help="run only the similarity section (for profiling)")
+    ap.add_argument("--sim-n", type=int, default=None, help="similarity series count")
     return ap.parse_args()
 
 
@@ -196,6 +200,79 @@ def measured_peaks():
             d = json.load(f)
         return d.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+def measured_bf16_tflops():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), "measured"
+    return 1900.0, 1700.0, "fallback"
+
+
+def run_similarity(T, ctx, stream, n_series=None):
+    """The Pearson similarity of raw series (n=30000, T=4096 random walks of
+    40 planted factors, float32): split-precision tensor-core products
+    (bf16x3, tf32x3) and the float SIMT path, each against the double path;
+    max/mean |delta rho| and the TMFG edge flips they cause (corr-tmfg P=1
+    on the leading 20000 series, the largest TMFG n of this build)."""
+    import torch
+    from paper_2408_09399_gb300 import workloads as W
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t0 = time.time()
+    X, _ = W.config_series(4, n=n_series)
+    gen_s = time.time() - t0
+    n, Tl = X.shape
+    Xd = torch.as_tensor(X, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    out, timing = {}, {}
+    pairs = n * (n + 1) / 2.0
+    for prec in ("bf16x3", "tf32x3", "f32", "f64"):
+        S = torch.empty((n, n), dtype=torch.float32, device=dev)
+        T.tmfg_similarity(ctx, Xd, prec, S=S, stream=stream)
+        T.tmfg_sync_status(ctx, stream)
+        reps = 1 if prec == "f64" else 3
+        ts = []
+        for _ in range(reps):
+            a, b = ev(), ev()
+            a.record(stream)
+            T.tmfg_similarity(ctx, Xd, prec, S=S, stream=stream)
+            b.record(stream)
+            ts.append((a, b))
+        T.tmfg_sync_status(ctx, stream)
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ts]))
+        products = 3 if prec.endswith("x3") else 1
+        flops = products * 2.0 * Tl * pairs
+        timing[prec] = {"ms": round(ms, 3), "tflops": round(flops / (ms * 1e-3) / 1e12, 1),
+                        "algorithmic_flops": flops}
+        out[prec] = S
+    ref = out["f64"]
+    nsub = min(n, T.tmfg_max_n(0))
+
+    def edges_of(S):
+        t = T.tmfg_build(ctx, S[:nsub, :nsub], "corr", 1, stream=stream)
+        T.tmfg_sync_status(ctx, stream)
+        e = t["edges"].cpu().numpy()
+        return {(int(min(a, b)), int(max(a, b))) for a, b in e}
+
+    e_ref = edges_of(ref)
+    for prec in ("bf16x3", "tf32x3", "f32"):
+        d = (out[prec] - ref).abs_()
+        timing[prec]["max_abs_drho"] = float(d.max().item())
+        timing[prec]["mean_abs_drho"] = float(d.mean(dtype=torch.float64).item())
+        del d
+        timing[prec]["tmfg_edge_flips"] = len(edges_of(out[prec]) ^ e_ref) // 2
+    peak, peak_sus, kind = measured_bf16_tflops()
+    bf = timing["bf16x3"]
+    roof = {"bound": "tensor", "kernel": "sim_tc_kernel<kind::f16> (bf16x3)",
+            "achieved": bf["tflops"], "peak": peak, "peak_kind": kind, "unit": "TFLOP/s",
+            "frac": round(bf["tflops"] / peak, 4), "traffic": None,
+            "tf32x3_frac": round(timing["tf32x3"]["tflops"] / (peak * 1.1 / 2.25), 4)}
+    return {"workload": f"n={n} T={Tl} random walks, 40 planted factors, float32",
+            "generation_s": round(gen_s, 1), "precisions": timing,
+            "tmfg_edge_flips_on": f"leading {nsub} series, corr-tmfg P=1, vs f64",
+            "roofline": roof}
 
 
 def run_ours(args, rank, world, local):
@@ -397,6 +474,8 @@ def run_ours(args, rank, world, local):
         result["batched"] = run_batched(T, ctx, args.batch_requests, stream)
     if not args.no_serve:
         result["serving"] = run_serving(T, ctx, args.serve_requests, stream)
+    if not args.no_sim:
+        result["similarity"] = run_similarity(T, ctx, stream, args.sim_n)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(S.cpu().numpy(), n)
     ctx.close()
@@ -693,7 +772,15 @@ def run_reference(args, rank, world):
 def main():
     args = parse()
     rank, world, local = dist_env()
-    if args.impl == "reference":
+    if args.sim_only:
+        import torch
+        import paper_2408_09399_gb300 as T
+        from paper_2408_09399_gb300 import build as B
+        B.build()
+        ctx = T.tmfg_create(local)
+        r = {"similarity": run_similarity(T, ctx, torch.cuda.current_stream(), args.sim_n)}
+        ctx.close()
+    elif args.impl == "reference":
         r = run_reference(args, rank, world)
     else:
         r = run_ours(args, rank, world, local)

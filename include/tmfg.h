@@ -227,6 +227,27 @@ int dbht_cluster_detail(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, int
                         const int32_t *bubble_parent, const float *D, int64_t ldd,
                         double *linkage, const dbht_outputs *out, void *stream);
 
+/* Precision of tmfg_similarity. */
+enum { TMFG_SIM_F64 = 0, TMFG_SIM_F32 = 1, TMFG_SIM_BF16X3 = 2, TMFG_SIM_TF32X3 = 3 };
+
+/* Pearson similarity matrix of n series (the input of the method, Section 5
+ * "Datasets": the Pearson correlation of every pair of time series).
+ *   X: n x T float32, row-major, contiguous (series i = X[i*T .. i*T+T-1]).
+ *   S: n x n float32 output, leading dimension ld >= n; S[i,j] = rho_ij,
+ *      exactly symmetric, diagonal exactly 1.
+ * Each series is centred and scaled to unit norm in double on the device;
+ * the products are then taken in the requested precision:
+ *   TMFG_SIM_F64     double dot products (CUDA cores; the accurate reference);
+ *   TMFG_SIM_F32     float dot products of the float-rounded series;
+ *   TMFG_SIM_BF16X3  y = hi + lo with bf16 halves, rho = hi.hi + hi.lo + lo.hi
+ *                    on the tensor cores (tcgen05, FP32 accumulation);
+ *   TMFG_SIM_TF32X3  the same with TF32 halves.
+ * A series that is constant or holds a NaN/infinity has no correlation:
+ * TMFG_ENONFINITE is recorded in the status word.  Workspace: about
+ * n*T*4 bytes (n*T*8 for F64 and TF32X3). */
+int tmfg_similarity(tmfg_ctx *ctx, const float *X, int64_t n, int64_t T, int32_t precision,
+                    float *S, int64_t ld, void *stream);
+
 /* ------------------------------------------------------------ serving
  * A request server with continuous batching (no counterpart in the paper).
  * Jobs (tmfg_job, buffers resident in device memory, caller-owned) are

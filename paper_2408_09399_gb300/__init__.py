@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "libtmfg.so")
 TMFG_F32, TMFG_F64 = 0, 1
 TMFG_CORR, TMFG_HEAP = 0, 1
 TMFG_CHECK_SYMMETRY = 1
+SIM_PRECISIONS = {"f64": 0, "f32": 1, "bf16x3": 2, "tf32x3": 3}
 ERRORS = {0: "TMFG_OK", 1: "TMFG_EINVAL", 2: "TMFG_ENOMEM", 3: "TMFG_ENONFINITE",
           4: "TMFG_EASYMMETRIC", 5: "TMFG_ETIMEOUT", 6: "TMFG_ECUDA", 7: "TMFG_ERANGE",
           8: "TMFG_ETOOBIG", 9: "TMFG_EINTERNAL"}
@@ -106,6 +107,8 @@ def load_library():
         lib.dbht_cluster_detail.argtypes = [P, P, i64, i64, i32, P, P, P, P, P, i64, P,
                                             ctypes.POINTER(_DbhtOutputs), P]
         lib.dbht_cluster_detail.restype = ctypes.c_int
+        lib.tmfg_similarity.argtypes = [P, P, i64, i64, i32, P, i64, P]
+        lib.tmfg_similarity.restype = ctypes.c_int
         lib.tmfg_serve_start.argtypes = [ctypes.POINTER(P), ctypes.c_int,
                                          ctypes.POINTER(_ServeConfig)]
         lib.tmfg_serve_start.restype = ctypes.c_int
@@ -277,6 +280,23 @@ def tmfg_apsp(ctx: Context, S, edges, approx: bool = False, n_hubs: int = 0,
                                   _dev_ptr(D, torch.float32), D.stride(0), _stream_handle(stream))
     _check(rc, "tmfg_apsp")
     return D
+
+
+def tmfg_similarity(ctx: Context, X, precision: str = "bf16x3", S=None, stream=None):
+    """Pearson similarity of the rows of X (float32 CUDA tensor, n x T,
+    contiguous) in the given precision ('f64', 'f32', 'bf16x3', 'tf32x3').
+    Returns S (float32, n x n)."""
+    torch = _torch()
+    if X.dim() != 2 or X.dtype != torch.float32 or not X.is_contiguous():
+        raise TypeError("X must be a contiguous float32 matrix")
+    n, T = X.shape
+    if S is None:
+        S = torch.empty((n, n), dtype=torch.float32, device=X.device)
+    rc = load_library().tmfg_similarity(ctx.handle, _dev_ptr(X), n, T, SIM_PRECISIONS[precision],
+                                        _dev_ptr(S, torch.float32), S.stride(0),
+                                        _stream_handle(stream))
+    _check(rc, "tmfg_similarity")
+    return S
 
 
 def _dbht_args(ctx, S, t, D):

@@ -1,5 +1,6 @@
 // api.cu -- the C ABI of libtmfg.so (declared in include/tmfg.h): context
 // and workspace management, argument checks, kernel launches.
+#include <climits>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -504,6 +505,21 @@ int tmfg_apsp(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, int32_t dtype
     if (rc) return rc;
     return launch_apsp(S, (int)n, ld, dtype, edges, approx, h, rf, D, ldd, ctx->work, ctx->status,
                        ctx->num_sms, ctx->timeout_ns, st);
+}
+
+int tmfg_similarity(tmfg_ctx *ctx, const float *X, int64_t n, int64_t T, int32_t precision,
+                    float *S, int64_t ld, void *stream)
+{
+    if (!ctx || !X || !S || n < 2 || T < 2 || ld < n || n > INT32_MAX / 2 || T > INT32_MAX / 2)
+        return TMFG_EINVAL;
+    if (precision < TMFG_SIM_F64 || precision > TMFG_SIM_TF32X3) return TMFG_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return TMFG_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = ensure_work(ctx, sim_work_bytes((int)n, (int)T, precision), st);
+    if (rc) return rc;
+    return launch_similarity(X, (int)n, (int)T, T, precision, S, ld, ctx->work, ctx->status,
+                             ctx->timeout_ns, st);
 }
 
 int dbht_cluster_detail(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, int32_t dtype,

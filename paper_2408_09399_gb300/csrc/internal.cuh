@@ -91,6 +91,12 @@ int launch_apsp(const void *S, int n, long long ld, int dtype, const int *edges,
 
 constexpr size_t kSmemLimit = 232448;  // 227 KB opt-in shared memory per CTA
 
+// similarity.cu
+long long sim_ldy(int T, int prec);
+size_t sim_work_bytes(int n, int T, int prec);
+int launch_similarity(const float *X, int n, int T, long long ldx, int prec, float *S, long long ld,
+                      void *work, int *status, unsigned long long timeout_ns, cudaStream_t stream);
+
 // dbht.cu
 size_t dbht_smem_bytes(int n);
 size_t dbht_work_bytes(int n);

@@ -158,7 +158,23 @@ CONFIGS = {
             dtype=np.float32, seed=1002),
     3: dict(n=20000, T=2000, k=50, sizes="dirichlet", loading=(0.3, 0.9), noise="t4",
             dtype=np.float32, seed=1003),
+    # raw series for the similarity product: random walks of 40 factors
+    4: dict(n=30000, T=4096, k=40, sizes="equal", loading=(0.3, 0.9), noise="normal",
+            dtype=np.float32, seed=1004, walk=True),
 }
+
+
+def config_series(cfg: int, n: int | None = None, T: int | None = None):
+    """(X float32 n x T, labels) of workload ``cfg`` (raw series; ``n`` and
+    ``T`` optionally shrink it)."""
+    c = dict(CONFIGS[cfg])
+    if n is not None:
+        c["n"] = n
+    if T is not None:
+        c["T"] = T
+    X, lab = factor_series(c["seed"], c["n"], c["T"], c["k"], c["sizes"], c["loading"],
+                           c["noise"], walk=c.get("walk", False), dtype=np.float32)
+    return X, lab
 
 
 def config_similarity(cfg: int, device: str = "cpu", n: int | None = None):

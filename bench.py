@@ -460,7 +460,12 @@ def run_ours(args, rank, world, local):
                    "parallelism": f"replicas x{world}"},
         "phases": {k: round(v, 3) for k, v in phases.items()},
         "loop_ns_per_insertion": round(stats["loop_ns"] / max(1, n - 4), 1),
-        "loop_stats": stats,
+        "loop_stats": {**{k: v for k, v in stats.items() if k not in (
+            "cycles_extract", "cycles_validate", "cycles_resolve", "cycles_stale_scan",
+            "epoch_iters")},
+            "pointer_probes": stats["cycles_extract"],
+            "warp_refreshes": stats["cycles_validate"],
+            "warp_refresh_steps": stats["cycles_resolve"]},
         "tmfg_variants": alt,
         "dbht": dbht,
         "roofline": roofline,

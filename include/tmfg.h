@@ -350,9 +350,13 @@ int tmfg_sync_status(tmfg_ctx *ctx, void *stream);
  * scan chunks loaded, out[3] = insertion rounds, out[4] = loop time in ns
  * (device clock), out[5..7] = SM cycles spent recomputing faces, updating
  * the max indexes, and selecting pairs (heap: resolving the stale pops);
- * out[8..15] = a finer split of those cycles (push, refresh, gains,
- * extraction, validation, resolution, stale scan) and the number of epoch
- * iterations.  `count` <= 16 entries are written. */
+ * out[8..10] = a finer split of those cycles (push, refresh, gains);
+ * out[11..13] = heap: cycles of extraction, validation and resolution;
+ * corr: pointer probes (64 sorted ids each), the warp refreshes that
+ * followed a probe that found nothing, and their 256-id steps; out[14] =
+ * heap: stale
+ * scan cycles; out[15] = heap: epoch iterations.  `count` <= 16 entries are
+ * written. */
 int tmfg_last_stats(tmfg_ctx *ctx, int64_t *out, int count);
 
 /* Static description of a return code. */

@@ -18,9 +18,10 @@
 //
 // MaxCorrs[w] is read fresh: the cached Mc[w] is kept while uninserted, else
 // the lazily advanced pointer of Section 4.3 moves on -- first one thread
-// probes the next 16 sorted ids (two 16-byte reads) against the inserted
-// bitmap, and only rows whose probe finds nothing go to a warp that scans
-// 256 sorted ids per step with 16-byte loads and a ballot.  A face's best
+// probes the next 64 sorted ids (eight 16-byte loads in flight, the 64
+// inserted-bitmap checks independent of one another), and only rows whose
+// probe finds nothing go to a warp that scans 256 sorted ids per step with
+// 16-byte loads and a ballot.  A face's best
 // vertex is computed by one thread: 9 independent gathers S[x,u] (3
 // candidates u x 3 face vertices x), gain = (S[a,u] + S[b,u]) + S[c,u] with
 // round-to-nearest adds in the dtype of S, ties to the smaller u.
@@ -196,12 +197,14 @@ __host__ __device__ inline LoopLayout loop_layout(int n, size_t ks, int ntrees)
     L.off_vlist = o; o = align16(o + 4 * (size_t)(3 * kChunk));
     L.off_vslow = o; o = align16(o + 4 * (size_t)(3 * kChunk));
     L.off_sel = o;   o = align16(o + ks * (size_t)kMaxPrefix);
-    L.off_x = o;     o = align16(o + 4 * (size_t)kXCap);
-    L.off_xkey = o;  o = align16(o + ks * (size_t)kXCap);
-    L.off_xpend = o; o = align16(o + ks * (size_t)kXCap);
-    L.off_xs = o;    o = align16(o + 2 * (size_t)kXCap);
-    L.off_q1x = o;   o = align16(o + 2 * (size_t)L.G1);
-    L.off_q2x = o;   o = align16(o + 2 * (size_t)64);
+    // the stale-pop resolution arrays exist in heap mode (two indexes) only
+    const size_t hx = ntrees > 1 ? 1 : 0;
+    L.off_x = o;     o = align16(o + hx * 4 * (size_t)kXCap);
+    L.off_xkey = o;  o = align16(o + hx * ks * (size_t)kXCap);
+    L.off_xpend = o; o = align16(o + hx * ks * (size_t)kXCap);
+    L.off_xs = o;    o = align16(o + hx * 2 * (size_t)kXCap);
+    L.off_q1x = o;   o = align16(o + hx * 2 * (size_t)L.G1);
+    L.off_q2x = o;   o = align16(o + hx * 2 * (size_t)64);
     L.total = o;
     return L;
 }
@@ -251,9 +254,12 @@ struct Loop {
     unsigned long long *pend_cand;
     // shared scalars
     int *nf, *k, *vcount, *vslow, *scan_chunks, *face_evals;
+    int *probes, *warp_refreshes, *warp_steps;
     long long cyc_push = 0, cyc_refresh = 0, cyc_gain = 0;  // thread 0's view
 
     __device__ bool is_ins(int v) const { return (ins[v >> 5] >> (v & 31)) & 1u; }
+    __device__ int fu_get(int i) const { return a.fu_buf[i]; }
+    __device__ void fu_put(int i, int e) { a.fu_buf[i] = e; }
 
     // Fresh MaxCorrs of vertex w (one warp): keep Mc[w] while uninserted,
     // else advance ptr[w] to the first uninserted entry of row w.  An id
@@ -281,7 +287,10 @@ struct Loop {
                 const int q = q0 + t;
                 if (q >= p && (q >= mlen || e[t] >= n || !is_ins(e[t]))) first = t;
             }
-            if (lane == 0) atomicAdd(scan_chunks, 1);
+            if (lane == 0) {
+                atomicAdd(scan_chunks, 1);
+                atomicAdd(warp_steps, 1);
+            }
             const unsigned bal = __ballot_sync(0xffffffffu, first < 8);
             if (bal) {
                 const int src = __ffs(bal) - 1;
@@ -329,32 +338,39 @@ struct Loop {
         }
         const uint16_t *row = a.idx + (long long)w * a.ldi;
         const int base = p & ~7;
-        uint4 c[2];
-        c[0] = *reinterpret_cast<const uint4 *>(row + base);
-        c[1] = base + 8 < a.ldi ? *reinterpret_cast<const uint4 *>(row + base + 8)
-                                : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+        uint4 c[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h)
+            c[h] = base + 8 * h < a.ldi ? *reinterpret_cast<const uint4 *>(row + base + 8 * h)
+                                        : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
         atomicAdd(scan_chunks, 1);
+        atomicAdd(probes, 1);
+        // all 64 checks independent (their shared-memory reads overlap); the
+        // first candidate wins
+        int first = 64, hit = kNone16;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const uint32_t wd[4] = {c[h].x, c[h].y, c[h].z, c[h].w};
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int q = base + 8 * h + t;
-                const int e = (wd[t >> 1] >> (16 * (t & 1))) & 0xFFFF;
-                if (q < p) continue;
-                if (q >= mlen || e >= n) {  // end of the row
-                    ptr[w] = (uint16_t)(q < mlen ? q : mlen);
-                    mc[w] = kNone16;
-                    return true;
-                }
-                if (!is_ins(e)) {
-                    ptr[w] = (uint16_t)q;
-                    mc[w] = (uint16_t)e;
-                    return true;
-                }
-            }
+        for (int j = 63; j >= 0; --j) {
+            const uint4 &cc = c[j >> 3];
+            const uint32_t wd = ((j >> 1) & 3) == 0 ? cc.x : ((j >> 1) & 3) == 1 ? cc.y
+                              : ((j >> 1) & 3) == 2 ? cc.z : cc.w;
+            const int e = (wd >> (16 * (j & 1))) & 0xFFFF;
+            const int q = base + j;
+            const bool stop = q >= mlen || e >= n;
+            const bool cand = q >= p && (stop || !is_ins(e));
+            if (cand) { first = j; hit = stop ? kNone16 : e; }
         }
-        ptr[w] = (uint16_t)(base + 15);  // all inserted up to here (base + 15 < mlen)
+        if (first < 64) {
+            const int q = base + first;
+            if (hit != kNone16) {
+                ptr[w] = (uint16_t)q;
+                mc[w] = (uint16_t)hit;
+            } else {
+                ptr[w] = (uint16_t)(q < mlen ? q : mlen);
+                mc[w] = kNone16;
+            }
+            return true;
+        }
+        ptr[w] = (uint16_t)(base + 63);  // all 64 inserted (so base + 63 < mlen)
         return false;
     }
 
@@ -398,11 +414,11 @@ struct Loop {
         atomicAdd(face_evals, 1);
     }
 
-    // Recompute the faces of list[0..cnt): entry = face | dest << 28.  The
-    // list may be in shared or global memory.  One thread per face, one
-    // thread per vertex to refresh (a warp per vertex when the first 16
-    // sorted ids are all inserted).  Ends synchronised.
-    __device__ void recompute(const int *list, int cnt)
+    // Recompute the faces of the face-update list [0..cnt): entry = face |
+    // dest << 28.  One thread per face, one thread per vertex to refresh (a
+    // warp per vertex when the first 64 sorted ids are all inserted).  Ends
+    // synchronised.
+    __device__ void recompute(int cnt)
     {
         const int tid = threadIdx.x, warp = tid >> 5;
         for (int c0 = 0; c0 < cnt; c0 += kChunk) {
@@ -413,7 +429,7 @@ struct Loop {
             int4 fc = make_int4(0, 0, 0, 0);
             int fe = 0;
             if (tid < m) {
-                fe = list[c0 + tid];
+                fe = fu_get(c0 + tid);
                 fc = a.face[fe & 0x0FFFFFFF];
                 const int vs[3] = {fc.x, fc.y, fc.z};
 #pragma unroll
@@ -433,6 +449,7 @@ struct Loop {
             }
             __syncthreads();
             const int ns = *vslow;
+            if (tid == 0) *warp_refreshes += ns;
             for (int i = warp; i < ns; i += kLoopWarps) refresh(vslowlist[i]);
             __syncthreads();
             long long c2t = clock64();
@@ -524,9 +541,10 @@ struct Loop {
 
     // Thread 0 only: insert v into face f; writes the outputs and the 3 new
     // faces (slot f, then nf, nf+1).
-    __device__ void insert_pair(int v, int f)
+    __device__ void insert_pair(int v, int f, bool have_face = false,
+                                int4 known = make_int4(0, 0, 0, 0))
     {
-        const int4 fc = a.face[f];
+        const int4 fc = have_face ? known : a.face[f];
         const int x = fc.x, y = fc.y, z = fc.z;
         const int kk = *k;
         const int nfc = *nf;
@@ -579,6 +597,7 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
     __shared__ int s_vslow;
     __shared__ int s_nf, s_k, s_vcount, s_scan, s_evals, s_stop, s_nsel, s_fcount;
     __shared__ int s_nx, s_ninv, s_nq1, s_np, s_more;
+    __shared__ int s_probes, s_wref, s_wsteps;
     __shared__ Key s_tau;
     __shared__ int s_clique[4];
     __shared__ long long s_red_r[kLoopWarps];
@@ -636,6 +655,9 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
     st.vslow = &s_vslow;
     st.scan_chunks = &s_scan;
     st.face_evals = &s_evals;
+    st.probes = &s_probes;
+    st.warp_refreshes = &s_wref;
+    st.warp_steps = &s_wsteps;
 
     const StateLayout SL = state_layout(n, sizeof(Key128));
     unsigned char *gs = reinterpret_cast<unsigned char *>(a.state);
@@ -666,6 +688,7 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
             const Key *gr = reinterpret_cast<const Key *>(gs + SL.off_roots);
             s_nf = (int)gscal[16]; s_k = (int)gscal[17];
             s_vcount = 0; s_scan = 0; s_evals = 0; s_stop = 0; s_nsel = 0; s_fcount = 0;
+            s_probes = 0; s_wref = 0; s_wsteps = 0;
             s_n1[0] = s_n1[1] = s_n2[0] = s_n2[1] = 0;
             s_root[0] = gr[0];
             s_root[1] = heap ? gr[1] : KO::empty();
@@ -697,6 +720,7 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
         if (heap) clear_tree(st.ts);
         if (tid == 0) {
             s_nf = 4; s_k = 0; s_vcount = 0; s_scan = 0; s_evals = 0; s_stop = 0; s_nsel = 0;
+            s_probes = 0; s_wref = 0; s_wsteps = 0;
             s_fcount = 0;
             s_n1[0] = s_n1[1] = s_n2[0] = s_n2[1] = 0;
             s_root[0] = s_root[1] = KO::empty();
@@ -750,13 +774,27 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
                 if (q > r) { t = q; q = r; r = t; }
                 if (p > q) { t = p; p = q; q = t; }
                 a.face[f] = make_int4(p, q, r, 0);
-                a.fu_buf[f] = f | (kToFresh << 28);
+                st.fu_put(f, f | (kToFresh << 28));
             }
         }
         __syncthreads();
-        st.recompute(a.fu_buf, 4);
+        st.recompute(4);
         st.update(heap);
     }
+
+    // thread 0 reads the face of the next root ahead of time (corr mode):
+    // the read overlaps the barriers before the insertion that uses it
+    int pf_f = -1;
+    int4 pf_fc = make_int4(0, 0, 0, 0);
+    auto prefetch_face = [&]() {
+        if (tid == 0 && !heap) {
+            const Key r = s_root[0];
+            pf_f = KO::is_empty(r) ? -1 : KO::face(r);
+            if (pf_f >= 0 && pf_f < L.nfmax) pf_fc = a.face[pf_f];
+            else pf_f = -1;
+        }
+    };
+    prefetch_face();
 
     // ---- main loop
     const int total = n - 4;
@@ -851,10 +889,10 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
                 // pending results still valid? (recompute the others)
                 for (int i = tid; i < nx; i += kLoopThreads) {
                     const int f = st.xf[i];
-                    if (!st.pend_valid(f)) a.fu_buf[atomicAdd(&s_ninv, 1)] = f | (kToPend << 28);
+                    if (!st.pend_valid(f)) st.fu_put(atomicAdd(&s_ninv, 1), f | (kToPend << 28));
                 }
                 __syncthreads();
-                if (s_ninv) st.recompute(a.fu_buf, s_ninv);
+                if (s_ninv) st.recompute(s_ninv);
                 long long e2 = clock64();
                 cyc_v += e2 - e1;
                 for (int i = tid; i < nx; i += kLoopThreads) {
@@ -912,9 +950,9 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
             const int nf_old = s_nf;
             if (tid == 0) {
                 st.insert_pair(v, fs);
-                a.fu_buf[0] = fs | (kToFresh << 28);
-                a.fu_buf[1] = nf_old | (kToFresh << 28);
-                a.fu_buf[2] = (nf_old + 1) | (kToFresh << 28);
+                st.fu_put(0, fs | (kToFresh << 28));
+                st.fu_put(1, nf_old | (kToFresh << 28));
+                st.fu_put(2, (nf_old + 1) | (kToFresh << 28));
                 s_fcount = 3;
             }
             __syncthreads();
@@ -932,7 +970,7 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
                             for (int b = 0; b < 2; ++b) {
                                 const int f = 8 * i + 2 * h + b;
                                 if (f < nf_old && f != fs && ((m >> (16 * b)) & 0xFFFFu))
-                                    a.fu_buf[atomicAdd(&s_fcount, 1)] = f | (kToPendMove << 28);
+                                    st.fu_put(atomicAdd(&s_fcount, 1), f | (kToPendMove << 28));
                             }
                         }
                     }
@@ -944,7 +982,7 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
                 cyc_scan += c - c_mark;
             }
             ++rounds;
-            st.recompute(a.fu_buf, s_fcount);
+            st.recompute(s_fcount);
             lap(cyc_rec);
             st.update(1);
             lap(cyc_tree);
@@ -986,7 +1024,8 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
                         continue;
                     }
                     st.rnd[v >> 5] |= 1u << (v & 31);
-                    st.insert_pair(v, KO::face(st.sel[i]));
+                    const int fsel = KO::face(st.sel[i]);
+                    st.insert_pair(v, fsel, i == 0 && fsel == pf_f, pf_fc);
                 }
                 s_fcount = 0;
             }
@@ -1012,7 +1051,7 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
                             for (int b = 0; b < 2; ++b) {
                                 const int f = 8 * i + 2 * h + b;
                                 if (f < nf_old && ((m >> (16 * b)) & 0xFFFFu))
-                                    a.fu_buf[atomicAdd(&s_fcount, 1)] = f | (kToFresh << 28);
+                                    st.fu_put(atomicAdd(&s_fcount, 1), f | (kToFresh << 28));
                             }
                         }
                     }
@@ -1021,13 +1060,13 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
                 for (int f = tid; f < nf_old; f += kLoopThreads) {
                     const int v = st.fv[f];
                     if (v != kNone16 && ((st.rnd[v >> 5] >> (v & 31)) & 1u))
-                        a.fu_buf[atomicAdd(&s_fcount, 1)] = f | (kToFresh << 28);
+                        st.fu_put(atomicAdd(&s_fcount, 1), f | (kToFresh << 28));
                 }
             }
             for (int f = nf_old + tid; f < nf_new; f += kLoopThreads)
-                a.fu_buf[atomicAdd(&s_fcount, 1)] = f | (kToFresh << 28);
+                st.fu_put(atomicAdd(&s_fcount, 1), f | (kToFresh << 28));
             __syncthreads();
-            st.recompute(a.fu_buf, s_fcount);
+            st.recompute(s_fcount);
             lap(cyc_rec);
             if (tid == 0)
                 for (int i = 0; i < nsel; ++i) {
@@ -1035,6 +1074,7 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
                     if (v < n) st.rnd[v >> 5] &= ~(1u << (v & 31));
                 }
             st.update(0);
+            prefetch_face();
             lap(cyc_tree);
         }
     }
@@ -1042,10 +1082,15 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
     __syncthreads();
     if (tid == 0) {
         if (s_stop) set_status(a.status, s_stop);
+        // slots 11..13: heap: cycles of extraction / validation / resolution;
+        // corr: pointer probes, warp refreshes after a probe found nothing,
+        // and the warp refreshes' 256-id steps
         const long long seg[16] = {s_evals, stale, s_scan, rounds,
                                    (long long)(globaltimer_ns() - t0), cyc_rec, cyc_tree, cyc_sel,
-                                   st.cyc_push, st.cyc_refresh, st.cyc_gain, cyc_x, cyc_v,
-                                   cyc_sim, cyc_scan, n_epoch_iters};
+                                   st.cyc_push, st.cyc_refresh, st.cyc_gain,
+                                   heap ? cyc_x : (long long)s_probes,
+                                   heap ? cyc_v : (long long)s_wref,
+                                   heap ? cyc_sim : (long long)s_wsteps, cyc_scan, n_epoch_iters};
         for (int i = 0; i < 16; ++i) {
             acc[i] += seg[i];
             a.stats[i] = acc[i];
@@ -1192,6 +1237,23 @@ size_t loop_smem_bytes(int n, int dtype, int mode)
     return loop_layout(n, ks, mode == TMFG_HEAP ? 2 : 1).total;
 }
 
+// The smallest shared-memory carve-out (percent of the SM's maximum) that
+// holds `ctas` CTAs of `smem` dynamic bytes (plus static and reserved
+// space): the rest of the unified L1/shared memory stays L1 cache, which
+// keeps recently probed sorted-row lines and faces close to the loop.
+int carveout_percent(size_t smem, int ctas)
+{
+    int dev = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+            cudaSuccess ||
+        per_sm <= 0)
+        return 100;
+    const size_t need = (size_t)ctas * (smem + 2048);
+    const size_t pct = (need * 100 + (size_t)per_sm - 1) / (size_t)per_sm;
+    return pct > 100 ? 100 : (int)pct;
+}
+
 // The insertion loop runs in segments; between them every sorted row is
 // compacted to its uninserted ids, so the lazy pointers keep finding an
 // uninserted id in their first probe.  Segments end after 1/2, 3/4, 7/8,
@@ -1202,8 +1264,11 @@ int launch_loop(const LoopArgs &args, int dtype, cudaStream_t stream)
     if (smem > kSmemLimit || 2 * (size_t)args.n - 4 > 65535) return TMFG_ETOOBIG;
     auto kf = tmfg_loop_kernel<float>;
     auto kd = tmfg_loop_kernel<double>;
-    if (cudaFuncSetAttribute(dtype == TMFG_F32 ? (const void *)kf : (const void *)kd,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    const void *kp = dtype == TMFG_F32 ? (const void *)kf : (const void *)kd;
+    if (cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(kp, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             carveout_percent(smem, 1)) != cudaSuccess)
         return TMFG_ECUDA;
     const int total = args.n - 4;
     int stops[8];
@@ -1240,8 +1305,11 @@ int launch_loop_batch(const LoopArgs *d_args, int count, int max_n, int dtype, i
     if (smem > kSmemLimit || 2 * (size_t)max_n - 4 > 65535) return TMFG_ETOOBIG;
     auto kf = tmfg_loop_batch_kernel<float>;
     auto kd = tmfg_loop_batch_kernel<double>;
-    if (cudaFuncSetAttribute(dtype == TMFG_F32 ? (const void *)kf : (const void *)kd,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    const void *kp = dtype == TMFG_F32 ? (const void *)kf : (const void *)kd;
+    if (cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(kp, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             carveout_percent(smem, 2)) != cudaSuccess)
         return TMFG_ECUDA;
     if (dtype == TMFG_F32)
         kf<<<count, kLoopThreads, smem, stream>>>(d_args);

@@ -258,6 +258,32 @@ struct Loop {
     long long cyc_push = 0, cyc_refresh = 0, cyc_gain = 0;  // thread 0's view
 
     __device__ bool is_ins(int v) const { return (ins[v >> 5] >> (v & 31)) & 1u; }
+
+    // Append to the face-update list every face f < nf whose stored vertex
+    // is v.  Eight stored vertices per 16-byte load; a branch-free test
+    // (some 16-bit lane of x ^ vv is zero) filters the loads, the exact
+    // per-lane comparison runs only on a hit.
+    __device__ void scan_faces_of(int v, int nf, int *count)
+    {
+        const uint32_t vv = (uint32_t)v | ((uint32_t)v << 16);
+        const uint4 *fv8 = reinterpret_cast<const uint4 *>(fv);
+        const int nq = (nf + 7) >> 3;
+        for (int i = threadIdx.x; i < nq; i += kLoopThreads) {
+            const uint4 q = fv8[i];
+            const uint32_t x0 = q.x ^ vv, x1 = q.y ^ vv, x2 = q.z ^ vv, x3 = q.w ^ vv;
+            auto z = [](uint32_t y) { return (y - 0x00010001u) & ~y & 0x80008000u; };
+            if (!(z(x0) | z(x1) | z(x2) | z(x3))) continue;  // no lane equals v
+            const uint32_t xs[4] = {x0, x1, x2, x3};
+#pragma unroll
+            for (int h = 0; h < 4; ++h)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const int f = 8 * i + 2 * h + b;
+                    if (f < nf && ((xs[h] >> (16 * b)) & 0xFFFFu) == 0)
+                        fu_put(atomicAdd(count, 1), f | (kToFresh << 28));
+                }
+        }
+    }
     __device__ int fu_get(int i) const { return a.fu_buf[i]; }
     __device__ void fu_put(int i, int e) { a.fu_buf[i] = e; }
 
@@ -809,7 +835,9 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
         c_mark = c;
     };
     while (s_k < k_stop) {
+        const int nf_top = s_nf;  // every thread reads it before thread 0 may change it
         if (tid == 0 && globaltimer_ns() - t0 > a.timeout_ns) s_stop = TMFG_ETIMEOUT;
+        if (tid == 0) s_fcount = 2;  // prefix 1: the two appended faces come first
         __syncthreads();
         if (s_stop) break;
         if (heap) {
@@ -987,6 +1015,37 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
             st.update(1);
             lap(cyc_tree);
         } else {
+            if (a.P == 1) {
+                // prefix 1: the pair is the root, known to every thread since
+                // the last index update.  Thread 0 inserts it while all
+                // threads list the faces whose stored vertex it is.
+                const Key r = s_root[0];
+                const int v = KO::is_empty(r) ? -1 : KO::vert(r);
+                const int fsel = KO::is_empty(r) ? -1 : KO::face(r);
+                if (v < 0 || v >= n || fsel >= nf_top || st.is_ins(v)) {
+                    if (tid == 0) s_stop = TMFG_EINTERNAL;
+                    __syncthreads();
+                    break;
+                }
+                lap(cyc_sel);
+                const int nf_old = nf_top;
+                if (tid == 0) {
+                    // the scan below reads stored vertices of faces < nf_old
+                    // only; the insertion writes the two new faces' entries
+                    st.insert_pair(v, fsel, fsel == pf_f, pf_fc);
+                    st.fu_put(0, nf_old | (kToFresh << 28));
+                    st.fu_put(1, (nf_old + 1) | (kToFresh << 28));
+                }
+                st.scan_faces_of(v, nf_old, &s_fcount);
+                __syncthreads();
+                ++rounds;
+                st.recompute(s_fcount);
+                lap(cyc_rec);
+                st.update(0);
+                prefetch_face();
+                lap(cyc_tree);
+                continue;
+            }
             // L = the P best pairs (repeated extraction from the index)
             if (tid == 0) s_nsel = 0;
             __syncthreads();

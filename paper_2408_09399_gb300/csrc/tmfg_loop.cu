@@ -66,6 +66,7 @@ constexpr int kLoopWarps = kLoopThreads / kWarp;
 constexpr int kChunk = kLoopThreads;  // faces per recompute batch (one per thread)
 constexpr int kMaxPrefix = 256;  // largest corr-tmfg prefix
 constexpr int kXCap = 256;       // stale faces resolved in one batch
+constexpr int kFuCap = 512;      // face-update list entries kept in shared memory
 
 // recompute destinations (encoded in bits 28..29 of a list entry)
 constexpr int kToFresh = 0;      // store as the face's key in the FRESH index
@@ -158,7 +159,7 @@ struct Tree {
 struct LoopLayout {
     int W, nfmax, G1, G2;
     size_t off_ins, off_vmark, off_rnd, off_mc, off_ptr, off_fv, off_tree[2], off_vlist, off_vslow,
-        off_sel, off_x, off_xkey, off_xpend, off_xs, off_q1x, off_q2x, total;
+        off_sel, off_x, off_xkey, off_xpend, off_xs, off_q1x, off_q2x, off_fus, total;
     size_t tree_bytes;
 };
 
@@ -205,6 +206,7 @@ __host__ __device__ inline LoopLayout loop_layout(int n, size_t ks, int ntrees)
     L.off_xs = o;    o = align16(o + hx * 2 * (size_t)kXCap);
     L.off_q1x = o;   o = align16(o + hx * 2 * (size_t)L.G1);
     L.off_q2x = o;   o = align16(o + hx * 2 * (size_t)64);
+    L.off_fus = o;   o = align16(o + 4 * (size_t)kFuCap);
     L.total = o;
     return L;
 }
@@ -284,8 +286,13 @@ struct Loop {
                 }
         }
     }
-    __device__ int fu_get(int i) const { return a.fu_buf[i]; }
-    __device__ void fu_put(int i, int e) { a.fu_buf[i] = e; }
+    int *fus;  // the face-update list's first kFuCap entries (the rest in a.fu_buf)
+    __device__ int fu_get(int i) const { return i < kFuCap ? fus[i] : a.fu_buf[i]; }
+    __device__ void fu_put(int i, int e)
+    {
+        if (i < kFuCap) fus[i] = e;
+        else a.fu_buf[i] = e;
+    }
 
     // Fresh MaxCorrs of vertex w (one warp): keep Mc[w] while uninserted,
     // else advance ptr[w] to the first uninserted entry of row w.  An id
@@ -612,7 +619,10 @@ struct Loop {
     }
 };
 
-template <typename T>
+// kHeap selects Algorithm 2 (heap-tmfg) or Algorithm 1 (corr-tmfg) at
+// compile time: each kernel holds only its own path, which keeps the code
+// that one SM runs for every insertion compact.
+template <typename T, bool kHeap>
 __device__ __forceinline__ void loop_body(const LoopArgs &a)
 {
     using KO = KeyOps<T>;
@@ -633,7 +643,7 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
     const int n = a.n;
     if (*(volatile int *)a.status != 0) return;  // an earlier step failed
     const uint64_t t0 = globaltimer_ns();
-    const bool heap = a.mode == TMFG_HEAP;
+    constexpr bool heap = kHeap;
     const LoopLayout L = loop_layout(n, sizeof(Key), heap ? 2 : 1);
 
     Loop<T> st{a};
@@ -666,6 +676,7 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
     bind(st.ts, 1, a.leaf_stale);
     st.vlist = reinterpret_cast<int *>(smem + L.off_vlist);
     st.vslowlist = reinterpret_cast<int *>(smem + L.off_vslow);
+    st.fus = reinterpret_cast<int *>(smem + L.off_fus);
     st.sel = reinterpret_cast<Key *>(smem + L.off_sel);
     st.xf = reinterpret_cast<int *>(smem + L.off_x);
     st.xkey = reinterpret_cast<Key *>(smem + L.off_xkey);
@@ -1182,20 +1193,20 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
 }
 
 // One instance per launch (the arguments by value).
-template <typename T>
+template <typename T, bool kHeap>
 __global__ void __launch_bounds__(kLoopThreads, 1) tmfg_loop_kernel(LoopArgs a)
 {
-    loop_body<T>(a);
+    loop_body<T, kHeap>(a);
 }
 
 // Many instances per launch: CTA b runs instance b (arguments in global memory).
-template <typename T>
+template <typename T, bool kHeap>
 __global__ void __launch_bounds__(kLoopThreads, 2) tmfg_loop_batch_kernel(const LoopArgs *args)
 {
     __shared__ LoopArgs s_args;
     if (threadIdx.x == 0) s_args = args[blockIdx.x];
     __syncthreads();
-    loop_body<T>(s_args);
+    loop_body<T, kHeap>(s_args);
 }
 
 // Between loop segments: drop the inserted ids from every sorted row.  Row
@@ -1321,8 +1332,9 @@ int launch_loop(const LoopArgs &args, int dtype, cudaStream_t stream)
 {
     const size_t smem = loop_smem_bytes(args.n, dtype, args.mode);
     if (smem > kSmemLimit || 2 * (size_t)args.n - 4 > 65535) return TMFG_ETOOBIG;
-    auto kf = tmfg_loop_kernel<float>;
-    auto kd = tmfg_loop_kernel<double>;
+    const bool heap = args.mode == TMFG_HEAP;
+    auto kf = heap ? tmfg_loop_kernel<float, true> : tmfg_loop_kernel<float, false>;
+    auto kd = heap ? tmfg_loop_kernel<double, true> : tmfg_loop_kernel<double, false>;
     const void *kp = dtype == TMFG_F32 ? (const void *)kf : (const void *)kd;
     if (cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess ||
@@ -1362,8 +1374,9 @@ int launch_loop_batch(const LoopArgs *d_args, int count, int max_n, int dtype, i
 {
     const size_t smem = loop_smem_bytes(max_n, dtype, mode);
     if (smem > kSmemLimit || 2 * (size_t)max_n - 4 > 65535) return TMFG_ETOOBIG;
-    auto kf = tmfg_loop_batch_kernel<float>;
-    auto kd = tmfg_loop_batch_kernel<double>;
+    const bool heap = mode == TMFG_HEAP;
+    auto kf = heap ? tmfg_loop_batch_kernel<float, true> : tmfg_loop_batch_kernel<float, false>;
+    auto kd = heap ? tmfg_loop_batch_kernel<double, true> : tmfg_loop_batch_kernel<double, false>;
     const void *kp = dtype == TMFG_F32 ? (const void *)kf : (const void *)kd;
     if (cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess ||

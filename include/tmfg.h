@@ -227,6 +227,33 @@ int dbht_cluster_detail(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, int
                         const int32_t *bubble_parent, const float *D, int64_t ldd,
                         double *linkage, const dbht_outputs *out, void *stream);
 
+/* Options of tmfg_solve_host; 0 fields take the defaults. */
+typedef struct {
+    int32_t n_hubs;       /* approximate APSP: 0 = ceil(sqrt(n)) */
+    float radius_factor;  /* approximate APSP: 0 = 2.0 */
+    int32_t row_blocks;   /* S is moved and sorted in this many row blocks; 0 = 8, at most 32 */
+} tmfg_solve_params;
+
+/* The whole step from HOST memory: S (host, n x n, leading dimension ld)
+ * is copied to the device in row blocks, each block's rows sorted as soon as
+ * it has arrived (Algorithm 1's sort overlaps the transfer); then the
+ * insertion loop; then the exact APSP (into D_exact) and the approximate
+ * APSP (into D_approx), each optional (NULL skips it), with leading
+ * dimension ldd.  The TMFG (order, edges, ins_face, bubble_parent) and the
+ * distances are written to HOST memory, each copied back while the next
+ * stage computes (a second, internal stream carries the copies).  Results
+ * are those of tmfg_build and tmfg_apsp.  Asynchronous and ordered on
+ * `stream` like every call: the host buffers are complete once the stream
+ * has reached the end of the call (tmfg_sync_status).  Host buffers should
+ * be page-locked (cudaHostAlloc or cudaHostRegister) for the copies to
+ * overlap; other host memory works but serialises them.  The device copies
+ * live in a second context block of about n*n*(4 + 4 + 4) bytes, within the
+ * context budget. */
+int tmfg_solve_host(tmfg_ctx *ctx, const void *S_host, int64_t n, int64_t ld,
+                    const tmfg_params *params, const tmfg_solve_params *sp, int32_t *order,
+                    int32_t *edges, int32_t *ins_face, int32_t *bubble_parent, float *D_exact,
+                    float *D_approx, int64_t ldd, void *stream);
+
 /* Precision of tmfg_similarity. */
 enum { TMFG_SIM_F64 = 0, TMFG_SIM_F32 = 1, TMFG_SIM_BF16X3 = 2, TMFG_SIM_TF32X3 = 3 };
 

@@ -69,6 +69,11 @@ class _ServeResult(ctypes.Structure):
                 ("t_done_ns", ctypes.c_int64)]
 
 
+class _SolveParams(ctypes.Structure):
+    _fields_ = [("n_hubs", ctypes.c_int32), ("radius_factor", ctypes.c_float),
+                ("row_blocks", ctypes.c_int32)]
+
+
 class _ApspParams(ctypes.Structure):
     _fields_ = [("approx", ctypes.c_int32), ("n_hubs", ctypes.c_int32),
                 ("radius_factor", ctypes.c_float)]
@@ -107,6 +112,9 @@ def load_library():
         lib.dbht_cluster_detail.argtypes = [P, P, i64, i64, i32, P, P, P, P, P, i64, P,
                                             ctypes.POINTER(_DbhtOutputs), P]
         lib.dbht_cluster_detail.restype = ctypes.c_int
+        lib.tmfg_solve_host.argtypes = [P, P, i64, i64, ctypes.POINTER(_Params),
+                                        ctypes.POINTER(_SolveParams), P, P, P, P, P, P, i64, P]
+        lib.tmfg_solve_host.restype = ctypes.c_int
         lib.tmfg_similarity.argtypes = [P, P, i64, i64, i32, P, i64, P]
         lib.tmfg_similarity.restype = ctypes.c_int
         lib.tmfg_serve_start.argtypes = [ctypes.POINTER(P), ctypes.c_int,
@@ -280,6 +288,48 @@ def tmfg_apsp(ctx: Context, S, edges, approx: bool = False, n_hubs: int = 0,
                                   _dev_ptr(D, torch.float32), D.stride(0), _stream_handle(stream))
     _check(rc, "tmfg_apsp")
     return D
+
+
+def tmfg_solve_host(ctx: Context, S, mode: str = "corr", prefix: int = 1, exact: bool = True,
+                    approx: bool = True, n_hubs: int = 0, radius_factor: float = 0.0,
+                    row_blocks: int = 0, check_symmetry: bool = False, out=None, stream=None):
+    """The whole step from host memory (see tmfg_solve_host in include/tmfg.h):
+    S is a CPU tensor (page-locked for overlapped copies); returns a dict of
+    CPU tensors order, edges, ins_face, bubble_parent and, when asked, D and
+    D_approx (float32, n x n).  Asynchronous: call tmfg_sync_status before
+    reading them."""
+    torch = _torch()
+    if S.is_cuda or S.dim() != 2 or S.shape[0] != S.shape[1] or S.stride(1) != 1:
+        raise ValueError("S must be a square row-major CPU matrix")
+    if S.dtype not in (torch.float32, torch.float64):
+        raise TypeError("S must be float32 or float64")
+    n = S.shape[0]
+    dt = TMFG_F32 if S.dtype == torch.float32 else TMFG_F64
+    if out is None:
+        pin = S.is_pinned()
+        out = {"order": torch.empty(n, dtype=torch.int32, pin_memory=pin),
+               "edges": torch.empty((3 * n - 6, 2), dtype=torch.int32, pin_memory=pin),
+               "ins_face": torch.empty((max(n - 4, 0), 3), dtype=torch.int32, pin_memory=pin),
+               "bubble_parent": torch.empty(n - 3, dtype=torch.int32, pin_memory=pin)}
+        if exact:
+            out["D"] = torch.empty((n, n), dtype=torch.float32, pin_memory=pin)
+        if approx:
+            out["D_approx"] = torch.empty((n, n), dtype=torch.float32, pin_memory=pin)
+    for k, v in out.items():
+        if v.is_cuda:
+            raise ValueError(f"{k} must be a CPU tensor")
+    D, Da = out.get("D"), out.get("D_approx")
+    ldd = (D if D is not None else Da).stride(0) if (D is not None or Da is not None) else n
+    p = _Params({"corr": TMFG_CORR, "heap": TMFG_HEAP}[mode], int(prefix), dt,
+                TMFG_CHECK_SYMMETRY if check_symmetry else 0)
+    sp = _SolveParams(int(n_hubs), float(radius_factor), int(row_blocks))
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+    rc = load_library().tmfg_solve_host(
+        ctx.handle, ptr(S), n, S.stride(0), ctypes.byref(p), ctypes.byref(sp), ptr(out["order"]),
+        ptr(out["edges"]), ptr(out["ins_face"]) if n > 4 else None, ptr(out["bubble_parent"]),
+        ptr(D), ptr(Da), ldd, _stream_handle(stream))
+    _check(rc, "tmfg_solve_host")
+    return out
 
 
 def tmfg_similarity(ctx: Context, X, precision: str = "bf16x3", S=None, stream=None):

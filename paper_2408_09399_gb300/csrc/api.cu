@@ -158,6 +158,75 @@ int check_symmetry(tmfg_ctx *c, const void *S, int64_t n, int64_t ld, int dtype,
 
 }  // namespace
 
+namespace {
+// The insertion loop of tmfg_build over rows already sorted into w.
+int launch_build_loop(tmfg_ctx *ctx, const BuildWork &w, const void *S, int64_t n, int64_t ld,
+                      const tmfg_params *params, int32_t *order, int32_t *edges,
+                      int32_t *ins_face, int32_t *bubble_parent, cudaStream_t st)
+{
+    const int dtype = params->dtype;
+    LoopArgs a{};
+    a.S = S;
+    a.ld = ld;
+    a.n = (int)n;
+    a.mode = params->mode;
+    a.P = params->prefix;
+    a.idx = w.idx;
+    a.ldi = ldi_for(n);
+    a.rowsum = w.rowsum;
+    a.order = order;
+    a.edges = edges;
+    a.ins_face = ins_face;
+    a.parent = bubble_parent;
+    a.face = w.face;
+    a.leaf_fresh = w.leaf_fresh;
+    a.leaf_stale = w.leaf_stale;
+    a.pend_key = w.pend_key;
+    a.pend_cand = w.pend_cand;
+    a.fu_buf = w.fu_buf;
+    a.state = w.state;
+    a.status = ctx->status;
+    a.stats = ctx->stats;
+    a.timeout_ns = ctx->timeout_ns;
+    return launch_loop(a, dtype, st);
+}
+
+// The device block of tmfg_solve_host (grown like the workspace).
+int ensure_io(tmfg_ctx *c, size_t bytes, cudaStream_t stream)
+{
+    if (bytes <= c->io_bytes) return TMFG_OK;
+    if (c->budget && c->work_bytes + bytes > c->budget) return TMFG_ENOMEM;
+    if (c->io) {
+        if (cudaStreamSynchronize(stream) != cudaSuccess) return TMFG_ECUDA;
+        cudaFree(c->io);
+        c->io = nullptr;
+        c->io_bytes = 0;
+    }
+    if (cudaMalloc(&c->io, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        c->io = nullptr;
+        return TMFG_ENOMEM;
+    }
+    c->io_bytes = bytes;
+    return TMFG_OK;
+}
+
+int ensure_copy_stream(tmfg_ctx *c)
+{
+    if (!c->cstream &&
+        cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking) != cudaSuccess)
+        return TMFG_ECUDA;
+    if (!c->ev_ready) {
+        for (cudaEvent_t &e : c->ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+                return TMFG_ECUDA;
+        c->ev_ready = true;
+    }
+    return TMFG_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int tmfg_create(tmfg_ctx **out, int device, size_t workspace_budget_bytes)
@@ -209,6 +278,10 @@ void tmfg_destroy(tmfg_ctx *ctx)
     if (ctx->status) cudaFree(ctx->status);
     if (ctx->stage) cudaFreeHost(ctx->stage);
     cudaEventDestroy(ctx->stage_ev);
+    if (ctx->io) cudaFree(ctx->io);
+    if (ctx->cstream) cudaStreamDestroy(ctx->cstream);
+    if (ctx->ev_ready)
+        for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -270,31 +343,10 @@ int tmfg_build(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, const tmfg_p
     rc = launch_rowsort(S, (int)n, ld, dtype, w.idx, ldi_for(n), w.rowsum, ctx->status,
                         ctx->num_sms, st);
     if (rc) return rc;
-    LoopArgs a{};
-    a.S = S;
-    a.ld = ld;
-    a.n = (int)n;
-    a.mode = params->mode;
-    a.P = params->prefix;
-    a.idx = w.idx;
-    a.ldi = ldi_for(n);
-    a.rowsum = w.rowsum;
-    a.order = order;
-    a.edges = edges;
-    a.ins_face = ins_face;
-    a.parent = bubble_parent;
-    a.face = w.face;
-    a.leaf_fresh = w.leaf_fresh;
-    a.leaf_stale = w.leaf_stale;
-    a.pend_key = w.pend_key;
-    a.pend_cand = w.pend_cand;
-    a.fu_buf = w.fu_buf;
-    a.state = w.state;
-    a.status = ctx->status;
-    a.stats = ctx->stats;
-    a.timeout_ns = ctx->timeout_ns;
-    return launch_loop(a, dtype, st);
+    return launch_build_loop(ctx, w, S, n, ld, params, order, edges, ins_face, bubble_parent, st);
 }
+
+
 
 int tmfg_batch_run(tmfg_ctx *ctx, const tmfg_job *jobs, int32_t count, const tmfg_params *params,
                    const tmfg_batch_config *cfg, void *stream)
@@ -551,6 +603,137 @@ int dbht_cluster(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, int32_t dt
 {
     return dbht_cluster_detail(ctx, S, n, ld, dtype, order, edges, ins_face, bubble_parent, D, ldd,
                                linkage, nullptr, stream);
+}
+
+int tmfg_solve_host(tmfg_ctx *ctx, const void *S_host, int64_t n, int64_t ld,
+                    const tmfg_params *params, const tmfg_solve_params *sp, int32_t *order,
+                    int32_t *edges, int32_t *ins_face, int32_t *bubble_parent, float *D_exact,
+                    float *D_approx, int64_t ldd, void *stream)
+{
+    if (!ctx || !S_host || !params || !order || !edges || !bubble_parent || n < 4 || ld < n)
+        return TMFG_EINVAL;
+    if (n > 4 && !ins_face) return TMFG_EINVAL;
+    if ((D_exact || D_approx) && ldd < n) return TMFG_EINVAL;
+    const int dtype = params->dtype;
+    if (dtype != TMFG_F32 && dtype != TMFG_F64) return TMFG_EINVAL;
+    if (params->mode != TMFG_CORR && params->mode != TMFG_HEAP) return TMFG_EINVAL;
+    if (params->prefix < 1 || params->prefix > kMaxPrefixApi) return TMFG_EINVAL;
+    if (params->mode == TMFG_HEAP && params->prefix != 1) return TMFG_EINVAL;
+    if (n > tmfg_max_n(dtype)) return TMFG_ETOOBIG;
+    const int h = hubs_for(n, sp ? sp->n_hubs : 0);
+    const float rf = (sp && sp->radius_factor > 0.0f) ? sp->radius_factor : 2.0f;
+    if (D_approx && (h < 1 || 4 * (n + h) > (int64_t)kSmemLimit - 1024)) return TMFG_EINVAL;
+    int blocks = sp && sp->row_blocks > 0 ? sp->row_blocks : 8;
+    if (blocks > 32) blocks = 32;
+    if (blocks > n) blocks = (int)n;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return TMFG_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = ensure_copy_stream(ctx);
+    if (rc) return rc;
+    cudaStream_t cs = ctx->cstream;
+    // one workspace for every stage (no reallocation between them)
+    size_t wb = build_work_bytes(n);
+    if (D_exact) wb = wb > apsp_work_bytes((int)n, 0, h) ? wb : apsp_work_bytes((int)n, 0, h);
+    if (D_approx) wb = wb > apsp_work_bytes((int)n, 1, h) ? wb : apsp_work_bytes((int)n, 1, h);
+    rc = ensure_work(ctx, wb, st);
+    if (rc) return rc;
+    // device block: S, D, D approx, then the TMFG outputs
+    const size_t esz = dtype == TMFG_F32 ? 4 : 8;
+    const size_t bS = round256((size_t)n * (size_t)ld * esz);
+    const size_t bD = round256((size_t)n * (size_t)n * 4);
+    const size_t bo = round256(4 * (size_t)n) + round256(8 * (3 * (size_t)n - 6)) +
+                      round256(12 * (size_t)(n > 4 ? n - 4 : 1)) + round256(4 * (size_t)n);
+    rc = ensure_io(ctx, bS + (D_exact ? bD : 0) + (D_approx ? bD : 0) + bo, st);
+    if (rc) return rc;
+    char *p = static_cast<char *>(ctx->io);
+    void *dS = p;
+    p += bS;
+    float *dD = D_exact ? reinterpret_cast<float *>(p) : nullptr;
+    p += D_exact ? bD : 0;
+    float *dDa = D_approx ? reinterpret_cast<float *>(p) : nullptr;
+    p += D_approx ? bD : 0;
+    int32_t *d_order = reinterpret_cast<int32_t *>(p);
+    p += round256(4 * (size_t)n);
+    int32_t *d_edges = reinterpret_cast<int32_t *>(p);
+    p += round256(8 * (3 * (size_t)n - 6));
+    int32_t *d_face = reinterpret_cast<int32_t *>(p);
+    p += round256(12 * (size_t)(n > 4 ? n - 4 : 1));
+    int32_t *d_parent = reinterpret_cast<int32_t *>(p);
+
+    cudaEvent_t *ev = ctx->ev;
+    auto fail = [](cudaError_t e) { return e != cudaSuccess; };
+    // copies wait for the compute stream's earlier work on these buffers
+    if (fail(cudaEventRecord(ev[0], st)) || fail(cudaStreamWaitEvent(cs, ev[0], 0)))
+        return TMFG_ECUDA;
+    BuildWork w = build_carve(ctx->work, n);
+    // S in row blocks: each block is sorted as soon as it has arrived
+    for (int b = 0; b < blocks; ++b) {
+        const int64_t r0 = n * b / blocks, r1 = n * (b + 1) / blocks;
+        const size_t off = (size_t)r0 * (size_t)ld * esz;
+        // rows r0..r1-1, reading no further than the last row's n elements
+        const size_t bytes = ((size_t)(r1 - r0 - 1) * (size_t)ld + (size_t)n) * esz;
+        if (fail(cudaMemcpyAsync(static_cast<char *>(dS) + off,
+                                 static_cast<const char *>(S_host) + off, bytes,
+                                 cudaMemcpyHostToDevice, cs)) ||
+            fail(cudaEventRecord(ev[1 + b], cs)) || fail(cudaStreamWaitEvent(st, ev[1 + b], 0)))
+            return TMFG_ECUDA;
+        rc = launch_rowsort(dS, (int)n, ld, dtype, w.idx, ldi_for(n), w.rowsum, ctx->status,
+                            ctx->num_sms, st, (int)r0, (int)r1);
+        if (rc) return rc;
+    }
+    if (params->flags & TMFG_CHECK_SYMMETRY) {
+        rc = check_symmetry(ctx, dS, n, ld, dtype, st);
+        if (rc) return rc;
+    }
+    rc = launch_build_loop(ctx, w, dS, n, ld, params, d_order, d_edges, d_face, d_parent, st);
+    if (rc) return rc;
+    // the TMFG goes back while the distances are computed
+    auto out_copy = [&](int e, void *dst, const void *src, size_t bytes) {
+        return fail(cudaEventRecord(ev[e], st)) || fail(cudaStreamWaitEvent(cs, ev[e], 0)) ||
+               fail(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, cs));
+    };
+    if (out_copy(33, order, d_order, 4 * (size_t)n) ||
+        fail(cudaMemcpyAsync(edges, d_edges, 8 * (3 * (size_t)n - 6), cudaMemcpyDeviceToHost, cs)) ||
+        (n > 4 && fail(cudaMemcpyAsync(ins_face, d_face, 12 * (size_t)(n - 4),
+                                       cudaMemcpyDeviceToHost, cs))) ||
+        fail(cudaMemcpyAsync(bubble_parent, d_parent, 4 * (size_t)(n - 3), cudaMemcpyDeviceToHost,
+                             cs)))
+        return TMFG_ECUDA;
+    // rows [r0, r1) of a distance matrix to the host, after the work on st so far
+    auto d_copy = [&](int e, float *dst, const float *src, int64_t r0, int64_t r1) {
+        if (fail(cudaEventRecord(ev[e], st)) || fail(cudaStreamWaitEvent(cs, ev[e], 0)))
+            return true;
+        if (ldd == n)  // one contiguous block: the plain copy runs at full link speed
+            return fail(cudaMemcpyAsync(dst + r0 * n, src + r0 * n, 4 * (size_t)n * (r1 - r0),
+                                        cudaMemcpyDeviceToHost, cs));
+        return fail(cudaMemcpy2DAsync(dst + r0 * ldd, 4 * (size_t)ldd, src + r0 * n, 4 * (size_t)n,
+                                      4 * (size_t)n, (size_t)(r1 - r0), cudaMemcpyDeviceToHost,
+                                      cs));
+    };
+    if (D_exact) {
+        // four pieces of sources: each piece's rows go back while the next computes
+        rc = launch_apsp_csr(dS, (int)n, ld, dtype, d_edges, ctx->work, ctx->status, st);
+        if (rc) return rc;
+        constexpr int kPieces = 4;
+        for (int b = 0; b < kPieces; ++b) {
+            const int64_t s0 = n * b / kPieces, s1 = n * (b + 1) / kPieces;
+            rc = launch_apsp_exact_rows((int)n, ctx->work, dD, n, (int)s0, (int)s1, ctx->status,
+                                        ctx->num_sms, ctx->timeout_ns, st);
+            if (rc) return rc;
+            if (d_copy(34 + b, D_exact, dD, s0, s1)) return TMFG_ECUDA;
+        }
+    }
+    if (D_approx) {
+        rc = launch_apsp(dS, (int)n, ld, dtype, d_edges, 1, h, rf, dDa, n, ctx->work,
+                         ctx->status, ctx->num_sms, ctx->timeout_ns, st);
+        if (rc) return rc;
+        if (d_copy(38, D_approx, dDa, 0, n)) return TMFG_ECUDA;
+    }
+    // the call completes on `stream` once every copy has
+    if (fail(cudaEventRecord(ev[39], cs)) || fail(cudaStreamWaitEvent(st, ev[39], 0)))
+        return TMFG_ECUDA;
+    return TMFG_OK;
 }
 
 int tmfg_sync_status(tmfg_ctx *ctx, void *stream)

@@ -146,7 +146,7 @@ __device__ __forceinline__ bool sssp_source(const SsspArgs &a, int i, uint64_t t
     {
         if (tid == 0) s_abort = (*(volatile int *)a.status != 0) ||
                                 (globaltimer_ns() - t0 > a.timeout_ns);
-        const int s = a.src ? a.src[i] : i;
+        const int s = a.src ? a.src[i] : a.src0 + i;
         for (int v = tid; v < n; v += NT) dist[v] = __int_as_float(0x7f800000);
         for (int w = tid; w < W; w += NT) { bm0[w] = 0; bm1[w] = 0; }
         __syncthreads();
@@ -485,6 +485,52 @@ ApspWork apsp_carve(void *base, int n, int approx, int h)
         w.DH = static_cast<float *>(take(4 * (size_t)h * n));
     }
     return w;
+}
+
+int launch_apsp_csr(const void *S, int n, long long ld, int dtype, const int *edges, void *work,
+                    int *status, cudaStream_t stream)
+{
+    const int ne = 3 * n - 6;
+    ApspWork w = apsp_carve(work, n, 0, 1);
+    if (cudaMemsetAsync(w.deg, 0, 4 * (size_t)n, stream) != cudaSuccess) return TMFG_ECUDA;
+    const int eb = (ne + 255) / 256;
+    csr_degree_kernel<<<eb, 256, 0, stream>>>(edges, ne, n, w.deg, status);
+    csr_scan_kernel<<<1, 1024, 0, stream>>>(w.deg, n, w.rowptr, w.cursor);
+    if (dtype == TMFG_F32)
+        csr_fill_kernel<float><<<eb, 256, 0, stream>>>(edges, ne, n, static_cast<const float *>(S),
+                                                       ld, w.cursor, w.arcs);
+    else
+        csr_fill_kernel<double><<<eb, 256, 0, stream>>>(edges, ne, n,
+                                                        static_cast<const double *>(S), ld,
+                                                        w.cursor, w.arcs);
+    return cudaGetLastError() == cudaSuccess ? TMFG_OK : TMFG_ECUDA;
+}
+
+int launch_apsp_exact_rows(int n, void *work, float *D, long long ldd, int s0, int s1, int *status,
+                           int num_sms, unsigned long long timeout_ns, cudaStream_t stream)
+{
+    ApspWork w = apsp_carve(work, n, 0, 1);
+    const size_t smem = sssp_smem_bytes(n);
+    if (smem > 232448) return TMFG_ETOOBIG;
+    if (cudaFuncSetAttribute(sssp_kernel<false, kSsspThreads>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return TMFG_ECUDA;
+    SsspArgs a{};
+    a.n = n;
+    a.rowptr = w.rowptr;
+    a.arcs = w.arcs;
+    a.status = status;
+    a.timeout_ns = timeout_ns;
+    a.src = nullptr;
+    a.src0 = s0;
+    a.nsrc = s1 - s0;
+    a.out = D + (long long)s0 * ldd;
+    a.ldo = ldd;
+    const int rows = s1 - s0;
+    if (rows <= 0) return TMFG_OK;
+    const int grid = rows < 2 * num_sms ? rows : 2 * num_sms;
+    sssp_kernel<false, kSsspThreads><<<grid, kSsspThreads, smem, stream>>>(a);
+    return cudaGetLastError() == cudaSuccess ? TMFG_OK : TMFG_ECUDA;
 }
 
 int launch_apsp(const void *S, int n, long long ld, int dtype, const int *edges, int approx,

@@ -18,6 +18,13 @@ struct tmfg_ctx {
     size_t stage_bytes;
     cudaEvent_t stage_ev; // recorded after the last copy out of the staging buffer
     bool stage_used;
+    // tmfg_solve_host: device copies of its inputs and outputs, a copy stream
+    // and the events that order the two streams
+    void *io;
+    size_t io_bytes;
+    cudaStream_t cstream;
+    cudaEvent_t ev[40];
+    bool ev_ready;
 };
 
 namespace tmfg {

@@ -19,8 +19,10 @@ int64_t rowsort_max_n(int dtype);
 size_t rowsort_smem(int n, int dtype);
 int launch_rowsort_batch(const SortJob *d_jobs, const int *d_row_begin, int njobs, int max_n,
                          int dtype, int *status, int grid, cudaStream_t stream);
+// rows [row0, row1) of the matrix (row1 < 0: to the last row)
 int launch_rowsort(const void *S, int n, long long ld, int dtype, uint16_t *idx, long long ldi,
-                   long long *rowsum, int *status, int num_sms, cudaStream_t stream);
+                   long long *rowsum, int *status, int num_sms, cudaStream_t stream,
+                   int row0 = 0, int row1 = -1);
 
 // tmfg_loop.cu
 struct LoopArgs {
@@ -60,7 +62,8 @@ struct SsspArgs {
     int n;
     const int *rowptr;
     const uint2 *arcs;
-    const int *src;      // sources (null: source i = i)
+    const int *src;      // sources (null: source i = src0 + i)
+    int src0;
     int nsrc;
     float *out;          // row i of the output = source src[i]
     long long ldo;
@@ -88,6 +91,13 @@ size_t sssp_smem_bytes(int n);
 int launch_apsp(const void *S, int n, long long ld, int dtype, const int *edges, int approx,
                 int h, float rf, float *D, long long ldd, void *work, int *status, int num_sms,
                 unsigned long long timeout_ns, cudaStream_t stream);
+// The exact APSP in pieces: the CSR of the TMFG once, then the rows of the
+// sources [s0, s1) (row s of D), so that finished rows can be moved while
+// the next piece computes.
+int launch_apsp_csr(const void *S, int n, long long ld, int dtype, const int *edges, void *work,
+                    int *status, cudaStream_t stream);
+int launch_apsp_exact_rows(int n, void *work, float *D, long long ldd, int s0, int s1, int *status,
+                           int num_sms, unsigned long long timeout_ns, cudaStream_t stream);
 
 constexpr size_t kSmemLimit = 232448;  // 227 KB opt-in shared memory per CTA
 

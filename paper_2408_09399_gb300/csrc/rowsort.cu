@@ -311,10 +311,11 @@ __device__ __forceinline__ void sort_row(const T *row, int n, int v, bool vec_in
 template <int I, typename T>
 __global__ void __launch_bounds__(kSortThreads, 1)
 rowsort_kernel(const T *__restrict__ S, int n, long long ld, bool vec_in, uint16_t *__restrict__ idx,
-               long long ldi, bool vec_out, long long *__restrict__ rowsum, int *status)
+               long long ldi, bool vec_out, long long *__restrict__ rowsum, int *status, int row0,
+               int row1)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    for (int v = blockIdx.x; v < n; v += gridDim.x)
+    for (int v = row0 + blockIdx.x; v < row1; v += gridDim.x)
         sort_row<I, T>(S + (long long)v * ld, n, v, vec_in, idx + (long long)v * ldi, ldi, vec_out,
                        rowsum ? rowsum + v : nullptr, status, smem);
 }
@@ -402,7 +403,8 @@ static int dispatch_items(int I, F &&f)
 
 template <typename T>
 static int launch_rowsort_t(const void *S, int n, long long ld, uint16_t *idx, long long ldi,
-                            long long *rowsum, int *status, int num_sms, cudaStream_t stream)
+                            long long *rowsum, int *status, int num_sms, int row0, int row1,
+                            cudaStream_t stream)
 {
     const int dtype = sizeof(T) == 4 ? TMFG_F32 : TMFG_F64;
     const int I = pick_items(n - 1, dtype);
@@ -410,7 +412,9 @@ static int launch_rowsort_t(const void *S, int n, long long ld, uint16_t *idx, l
     if (I < 0 || smem > (size_t)kSortSmemMax) return TMFG_ETOOBIG;
     const bool vec_out = (ldi % 8 == 0) && ((uintptr_t)idx % 16 == 0);
     const bool vec_in = (ld % (16 / sizeof(T)) == 0) && ((uintptr_t)S % 16 == 0);
-    const int grid = n < num_sms ? n : num_sms;
+    const int rows = row1 - row0;
+    if (rows <= 0) return TMFG_OK;
+    const int grid = rows < num_sms ? rows : num_sms;
     return dispatch_items<T>(I, [&](auto ic) {
         constexpr int II = decltype(ic)::value;
         auto k = rowsort_kernel<II, T>;
@@ -418,17 +422,21 @@ static int launch_rowsort_t(const void *S, int n, long long ld, uint16_t *idx, l
             cudaSuccess)
             return (int)TMFG_ECUDA;
         k<<<grid, kSortThreads, smem, stream>>>(static_cast<const T *>(S), n, ld, vec_in, idx, ldi,
-                                                 vec_out, rowsum, status);
+                                                 vec_out, rowsum, status, row0, row1);
         return cudaGetLastError() == cudaSuccess ? (int)TMFG_OK : (int)TMFG_ECUDA;
     });
 }
 
 int launch_rowsort(const void *S, int n, long long ld, int dtype, uint16_t *idx, long long ldi,
-                   long long *rowsum, int *status, int num_sms, cudaStream_t stream)
+                   long long *rowsum, int *status, int num_sms, cudaStream_t stream, int row0,
+                   int row1)
 {
+    if (row1 < 0) row1 = n;
     if (dtype == TMFG_F32)
-        return launch_rowsort_t<float>(S, n, ld, idx, ldi, rowsum, status, num_sms, stream);
-    return launch_rowsort_t<double>(S, n, ld, idx, ldi, rowsum, status, num_sms, stream);
+        return launch_rowsort_t<float>(S, n, ld, idx, ldi, rowsum, status, num_sms, row0, row1,
+                                       stream);
+    return launch_rowsort_t<double>(S, n, ld, idx, ldi, rowsum, status, num_sms, row0, row1,
+                                    stream);
 }
 
 int launch_rowsort_batch(const SortJob *d_jobs, const int *d_row_begin, int njobs, int max_n,

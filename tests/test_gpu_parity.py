@@ -262,3 +262,43 @@ def test_full_size_n20000(T, ctx):
     # end one rounding below the fold from s: compare within float rounding
     assert np.all(Das >= Dr * (1 - 1e-6))
     assert np.all(Das[Das < Dr] >= Dr[Das < Dr] * (1 - 1e-6))
+
+
+# ------------------------------------------------------------------ host entry point
+
+@pytest.mark.parametrize("n,dtype,blocks,pinned", [(600, np.float32, 0, True),
+                                                   (333, np.float64, 3, True),
+                                                   (200, np.float32, 32, False),
+                                                   (1500, np.float32, 1, True)])
+def test_solve_host_equals_device_calls(T, ctx, n, dtype, blocks, pinned):
+    """tmfg_solve_host (host buffers, row-block pipelined copies) gives the
+    same TMFG and distances as tmfg_build + tmfg_apsp on the device."""
+    S_np = W.random_similarity(7000 + n, n, dtype)
+    S_h = torch.as_tensor(S_np)
+    if pinned:
+        S_h = S_h.pin_memory()
+    out = T.tmfg_solve_host(ctx, S_h, "corr", 1, row_blocks=blocks)
+    T.tmfg_sync_status(ctx)
+    dS = dev(S_np)
+    ref = T.tmfg_build(ctx, dS, "corr", 1)
+    D = T.tmfg_apsp(ctx, dS, ref["edges"])
+    Da = T.tmfg_apsp(ctx, dS, ref["edges"], approx=True)
+    T.tmfg_sync_status(ctx)
+    for k in ("order", "edges", "ins_face", "bubble_parent"):
+        assert np.array_equal(out[k].numpy(), ref[k].cpu().numpy()), k
+    assert np.array_equal(out["D"].numpy(), D.cpu().numpy())
+    assert np.array_equal(out["D_approx"].numpy(), Da.cpu().numpy())
+
+
+def test_solve_host_strided_and_partial(T, ctx):
+    n = 400
+    S_np = W.random_similarity(71, n, np.float32)
+    big = np.zeros((n, n + 5), np.float32)
+    big[:, :n] = S_np
+    S_h = torch.as_tensor(big)[:, :n]
+    out = T.tmfg_solve_host(ctx, S_h, "heap", 1, approx=False)
+    T.tmfg_sync_status(ctx)
+    ref = oracle.tmfg(S_np, "heap")
+    assert np.array_equal(out["edges"].numpy(), ref["edges"])
+    assert "D_approx" not in out
+    assert np.array_equal(out["D"].numpy(), oracle.apsp_exact(S_np, ref["edges"], prec=32))

@@ -202,6 +202,12 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+# DRAM bytes of one full-size corr-tmfg P=1 build of the loop kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum over its 6 segments, one ncu
+# capture of the current kernel at n = 20000; profiles/tmfg_loop_dram_n20000.md)
+LOOP_DRAM_BYTES_N20000 = 406_803_710
+
+
 def measured_bf16_tflops():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -409,7 +415,8 @@ def run_ours(args, rank, world, local):
                 "kernel": "tmfg_loop_kernel (the 6 segments of one build, with the 5 row "
                           "compactions between them)",
                 "achieved": round(loop_gbs, 2), "peak": hbm_peak, "peak_kind": peak_kind,
-                "unit": "GB/s", "frac": round(loop_gbs / hbm_peak, 5), "traffic": None,
+                "unit": "GB/s", "frac": round(loop_gbs / hbm_peak, 5),
+                "traffic": LOOP_DRAM_BYTES_N20000 if n == 20000 else None,
                 "algorithmic_bytes": int(loop_bytes), "ms": round(loop_ev_ms, 3),
                 "note": "dependent-latency chain of n-4 insertions (ns per insertion in "
                         "loop_ns_per_insertion); no roof binds it",

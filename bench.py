@@ -203,8 +203,8 @@ def measured_peaks():
 
 
 # DRAM bytes of one full-size corr-tmfg P=1 build of the loop kernel
-# (dram__bytes_read.sum + dram__bytes_write.sum over its 6 segments, one ncu
-# capture of the current kernel at n = 20000; profiles/tmfg_loop_dram_n20000.md)
+# (dram__bytes_read.sum + dram__bytes_write.sum over its 6 segments, from one
+# one-pass ncu capture of the current kernel at n = 20000)
 LOOP_DRAM_BYTES_N20000 = 406_803_710
 
 

@@ -16,21 +16,24 @@
 // Only the tiles on or above the diagonal are computed; each value is written
 // to (i,j) and (j,i), so S is exactly symmetric, and the diagonal is 1.
 //
-// Tensor-core kernel: one CTA (4 warps) per 128 x 128 output tile.  Warp 0
-// lane 0 streams 128-byte-wide K slices of the four operand tiles (A hi/lo,
-// B hi/lo) into shared memory with TMA (128-byte swizzle), three stages
-// deep, each stage guarded by a "full" and an "empty" mbarrier; warp 1 owns
-// four tensor-memory accumulators (128 columns each, all 512) and lane 0
-// issues the MMAs (4 K steps x 3 products per slice, slice k into
-// accumulator k mod 4) and commits each slice's completion to its "empty"
-// barrier; after the last slice a commit to the "accumulator" barrier
-// releases the epilogue, in which each warp reads its 32 rows of the four
-// accumulators (tcgen05.ld 32x32b) and adds them in FP32 (FP64 is slow on
-// this part); the tile is staged in the idle pipeline buffers and written,
-// with its transpose, in coalesced 128-byte rows.  The tensor core's FP32 accumulation
+// Tensor-core kernel: persistent, one CTA per SM, walking 128 x 128 output
+// tiles on or above the diagonal.  Warp 0 lane 0 streams 128-byte-wide K
+// slices of the four operand tiles (A hi/lo, B hi/lo) into shared memory
+// with TMA (128-byte swizzle), three stages deep, across tile boundaries,
+// each stage guarded by a "full" and an "empty" mbarrier.  Warp 1 owns the
+// tensor memory (512 columns: two tiles' accumulators, two accumulators of
+// 128 columns each per tile) and lane 0 issues the MMAs (4 K steps x 3
+// products per slice, slice k into accumulator k mod 2) and commits each
+// slice's completion to its "empty" barrier and each tile's to its buffer's
+// "full" barrier.  Warps 2..5 drain a finished buffer while the next tile
+// accumulates into the other: tcgen05.ld 32x32b of their 32 rows, the two
+// accumulators added in FP32, rows stored as 16-byte vectors and the
+// transpose with consecutive lanes on consecutive addresses; then the
+// buffer's "drained" barrier.  The tensor core's FP32 accumulation
 // truncates, so its error grows with the number of accumulation steps and
-// the size of the partial sums; four accumulators quarter both.  Every mbarrier wait is bounded by the device clock; a wait that
-// runs out records TMFG_ETIMEOUT, and the CTA still frees its tensor memory.
+// the size of the partial sums; two accumulators halve both.  Every
+// mbarrier wait is bounded by the device clock; a wait that runs out
+// records TMFG_ETIMEOUT, and the CTA still frees its tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -45,8 +48,9 @@ constexpr int kStages = 3;
 constexpr int kRowBytes = 128;    // bytes of one K slice of one row
 constexpr int kOpBytes = kTile * kRowBytes;  // one operand tile slice: 16 KB
 constexpr int kStageBytes = 4 * kOpBytes;    // A hi, A lo, B hi, B lo
-constexpr int kTcThreads = 128;
-constexpr int kAcc = 4;           // accumulators (128 TMEM columns each)
+constexpr int kTcThreads = 192;   // warp 0: TMA, warp 1: MMA, warps 2..5: epilogue
+constexpr int kAcc = 2;           // accumulators per tile (128 TMEM columns each)
+constexpr int kBufCols = kAcc * kTile;  // one tile's accumulators; two tiles in flight
 constexpr size_t kTcSmem = kStages * kStageBytes + 1024 + 256;
 
 // --------------------------------------------------------------- prep
@@ -245,6 +249,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_
     }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
                                             uint32_t bar)
 {
@@ -304,35 +313,41 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
 template <bool kTf32>
 __global__ void __launch_bounds__(kTcThreads, 1)
     sim_tc_kernel(const __grid_constant__ CUtensorMap map_hi,
-                  const __grid_constant__ CUtensorMap map_lo, int n, int kblocks, float *S,
-                  long long ld, int *status, unsigned long long timeout_ns)
+                  const __grid_constant__ CUtensorMap map_lo, int n, int kblocks, int tiles,
+                  float *S, long long ld, bool vec, int *status, unsigned long long timeout_ns)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
-    // bars[0..S): full, bars[S..2S): empty, bars[2S]: accumulator
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 1);
+    // bars[0..S): stage full, [S..2S): stage empty, [2S..2S+2): accumulator
+    // buffer full, [2S+2..2S+4): accumulator buffer drained
+    uint64_t *full = bars, *empty = bars + kStages, *tfull = bars + 2 * kStages,
+             *tempty = bars + 2 * kStages + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 4);
     __shared__ int s_abort;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nt = (n + kTile - 1) / kTile;
-    int I, J;
-    tri_tile_grouped<16>(blockIdx.x, nt, I, J);
     constexpr int kElems = kTf32 ? 32 : 64;  // elements per 128-byte K slice
     constexpr uint32_t kIdesc = idesc_128x128(kTf32 ? 2u : 1u);
     const uint64_t deadline = globaltimer_ns() + timeout_ns;
+    auto give_up = [&]() {
+        set_status(status, TMFG_ETIMEOUT);
+        s_abort = 1;
+    };
 
     if (threadIdx.x == 0) {
         s_abort = *status != 0;
-        for (int s = 0; s < 2 * kStages + 1; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        for (int s = 0; s < 2 * kStages + 2; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        for (int b = 0; b < 2; ++b) mbar_init(smem_u32(&tempty[b]), 4);  // 4 epilogue warps
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile(
             "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                 smem_u32(tmem_slot)),
-            "r"(kAcc * kTile)
+            "r"(2 * kBufCols)
             : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -342,131 +357,147 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t tmem = *tmem_slot;
     const bool skip = s_abort != 0;
 
-    if (!skip && warp == 0 && lane == 0) {
-        // producer
-        for (int kb = 0; kb < kblocks; ++kb) {
-            const int s = kb % kStages;
-            if (kb >= kStages &&
-                !mbar_wait(smem_u32(&bars[kStages + s]), ((kb / kStages) & 1) ^ 1, deadline)) {
-                set_status(status, TMFG_ETIMEOUT);
-                s_abort = 1;
-                break;
+    if (!skip && warp == 0) {
+        if (lane == 0) {  // producer: the K slices of this CTA's tiles, back to back
+            int it = 0;
+            for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+                int I, J;
+                tri_tile_grouped<16>(t, nt, I, J);
+                bool ok = true;
+                for (int kb = 0; kb < kblocks; ++kb, ++it) {
+                    const int s = it % kStages;
+                    if (it >= kStages &&
+                        !mbar_wait(smem_u32(&empty[s]), ((it / kStages) & 1) ^ 1, deadline)) {
+                        give_up();
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t fb = smem_u32(&full[s]);
+                    uint8_t *st = smem + s * kStageBytes;
+                    mbar_expect_tx(fb, kStageBytes);
+                    tma_load_2d(smem_u32(st), &map_hi, kb * kElems, I * kTile, fb);
+                    tma_load_2d(smem_u32(st + kOpBytes), &map_lo, kb * kElems, I * kTile, fb);
+                    tma_load_2d(smem_u32(st + 2 * kOpBytes), &map_hi, kb * kElems, J * kTile, fb);
+                    tma_load_2d(smem_u32(st + 3 * kOpBytes), &map_lo, kb * kElems, J * kTile, fb);
+                }
+                if (!ok || *(volatile int *)&s_abort) break;
             }
-            const uint32_t full = smem_u32(&bars[s]);
-            uint8_t *st = smem + s * kStageBytes;
-            mbar_expect_tx(full, kStageBytes);
-            tma_load_2d(smem_u32(st), &map_hi, kb * kElems, I * kTile, full);
-            tma_load_2d(smem_u32(st + kOpBytes), &map_lo, kb * kElems, I * kTile, full);
-            tma_load_2d(smem_u32(st + 2 * kOpBytes), &map_hi, kb * kElems, J * kTile, full);
-            tma_load_2d(smem_u32(st + 3 * kOpBytes), &map_lo, kb * kElems, J * kTile, full);
         }
-    } else if (!skip && warp == 1 && lane == 0) {
-        // MMA issuer
-        bool ok = true;
-        for (int kb = 0; kb < kblocks; ++kb) {
-            const int s = kb % kStages;
-            if (!mbar_wait(smem_u32(&bars[s]), (kb / kStages) & 1, deadline)) {
-                set_status(status, TMFG_ETIMEOUT);
-                s_abort = 1;
-                ok = false;
+    } else if (!skip && warp == 1) {
+        if (lane == 0) {  // MMA issuer: tile lt into accumulator buffer lt & 1
+            int it = 0, lt = 0;
+            for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++lt) {
+                const int buf = lt & 1;
+                if (lt >= 2 &&
+                    !mbar_wait(smem_u32(&tempty[buf]), ((lt >> 1) & 1) ^ 1, deadline)) {
+                    give_up();
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t accb = tmem + (uint32_t)(buf * kBufCols);
+                bool ok = true;
+                for (int kb = 0; kb < kblocks; ++kb, ++it) {
+                    const int s = it % kStages;
+                    if (!mbar_wait(smem_u32(&full[s]), (it / kStages) & 1, deadline)) {
+                        give_up();
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t st = smem_u32(smem + s * kStageBytes);
+                    const uint32_t acc = accb + (uint32_t)((kb % kAcc) * kTile);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t ah = sw128_desc(st + kk * 32);
+                        const uint64_t al = sw128_desc(st + kOpBytes + kk * 32);
+                        const uint64_t bh = sw128_desc(st + 2 * kOpBytes + kk * 32);
+                        const uint64_t bl = sw128_desc(st + 3 * kOpBytes + kk * 32);
+                        mma_issue<kTf32>(acc, ah, bh, kIdesc, (kb >= kAcc || kk != 0) ? 1u : 0u);
+                        mma_issue<kTf32>(acc, ah, bl, kIdesc, 1u);
+                        mma_issue<kTf32>(acc, al, bh, kIdesc, 1u);
+                    }
+                    mma_commit(smem_u32(&empty[s]));
+                }
+                if (!ok || *(volatile int *)&s_abort) break;
+                mma_commit(smem_u32(&tfull[buf]));  // completes once the tile's MMAs have
+            }
+        }
+    } else if (!skip) {
+        // epilogue warps 2..5: warp w reads TMEM lanes 32*(w % 4) .. +31 (its
+        // rows of the tile); row stores as 16-byte vectors where aligned, the
+        // transpose with consecutive lanes on consecutive addresses
+        const int q = warp & 3;
+        const int r = 32 * q + lane;
+        const int nacc = kblocks < kAcc ? kblocks : kAcc;
+        int lt = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++lt) {
+            const int buf = lt & 1;
+            bool ok = mbar_wait(smem_u32(&tfull[buf]), (lt >> 1) & 1, deadline);
+            ok = __all_sync(0xffffffffu, ok && !*(volatile int *)&s_abort);
+            if (!ok) {
+                if (lane == 0 && !*(volatile int *)&s_abort) give_up();
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t st = smem_u32(smem + s * kStageBytes);
-            const uint32_t acc = tmem + (uint32_t)((kb % kAcc) * kTile);  // column offset
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const uint64_t ah = sw128_desc(st + kk * 32);
-                const uint64_t al = sw128_desc(st + kOpBytes + kk * 32);
-                const uint64_t bh = sw128_desc(st + 2 * kOpBytes + kk * 32);
-                const uint64_t bl = sw128_desc(st + 3 * kOpBytes + kk * 32);
-                mma_issue<kTf32>(acc, ah, bh, kIdesc, (kb >= kAcc || kk != 0) ? 1u : 0u);
-                mma_issue<kTf32>(acc, ah, bl, kIdesc, 1u);
-                mma_issue<kTf32>(acc, al, bh, kIdesc, 1u);
-            }
-            mma_commit(smem_u32(&bars[kStages + s]));
-        }
-        // the accumulator barrier completes once every issued MMA has
-        if (ok) mma_commit(smem_u32(&bars[2 * kStages]));
-    }
-    __syncwarp();
-
-    // epilogue: warp w holds rows 32w..32w+31 of the tile (TMEM lanes)
-    bool have = false;
-    if (!skip) {
-        // a wait that runs out (or an abort elsewhere) skips the stores
-        have = mbar_wait(smem_u32(&bars[2 * kStages]), 0, deadline);
-        if (!have && lane == 0) set_status(status, TMFG_ETIMEOUT);
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    have = __syncthreads_and(have && !s_abort);  // CTA-uniform (tcgen05.ld is .sync.aligned)
-    // the pipeline buffers are idle now: stage the tile there, 129 floats a
-    // row so that row and column reads both hit 32 distinct banks
-    float *tile = reinterpret_cast<float *>(smem);
-    constexpr int kLd = kTile + 1;
-    if (have) {
-        const int r = warp * 32 + lane;
-        const int nacc = kblocks < kAcc ? kblocks : kAcc;
-#pragma unroll 1
-        for (int c0 = 0; c0 < kTile; c0 += 16) {
-            float sum[16];
-#pragma unroll 1
-            for (int a = 0; a < nacc; ++a) {
-                uint32_t v[16];
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, "
-                    "%9, %10, %11, %12, %13, %14, %15}, [%16];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                      "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-                      "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                    : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * kTile + c0)));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                for (int u = 0; u < 16; ++u)
-                    sum[u] = a ? __fadd_rn(sum[u], __uint_as_float(v[u])) : __uint_as_float(v[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < 16; ++u) tile[r * kLd + c0 + u] = sum[u];
-        }
-    }
-    __syncthreads();
-    if (have) {
-        // rows of the tile: S[I*128 + r, J*128 + c]; on a diagonal tile the
-        // lower half mirrors the upper (only values with row < column are used)
-        for (int r = warp; r < kTile; r += 4) {
+            int I, J;
+            tri_tile_grouped<16>(t, nt, I, J);
             const int gi = I * kTile + r;
-            if (gi >= n) continue;
+            const uint32_t accb =
+                tmem + (uint32_t)(buf * kBufCols) + ((uint32_t)(32 * q) << 16);
+#pragma unroll 1
+            for (int c0 = 0; c0 < kTile; c0 += 16) {
+                float sum[16];
+#pragma unroll 1
+                for (int a = 0; a < nacc; ++a) {
+                    uint32_t v[16];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, "
+                        "%8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]),
+                          "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]),
+                          "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                          "=r"(v[15])
+                        : "r"(accb + (uint32_t)(a * kTile + c0)));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int q = 0; q < kTile / 32; ++q) {
-                const int c = lane + 32 * q;
-                const int gj = J * kTile + c;
-                if (gj >= n) continue;
-                float x;
-                if (I != J || r < c) x = tile[r * kLd + c];
-                else if (r > c) x = tile[c * kLd + r];
-                else x = 1.0f;
-                S[(long long)gi * ld + gj] = x;
-            }
-        }
-        if (I != J) {
-            // the transpose: S[J*128 + c, I*128 + r]
-            for (int c = warp; c < kTile; c += 4) {
-                const int gj = J * kTile + c;
-                if (gj >= n) continue;
+                    for (int u = 0; u < 16; ++u)
+                        sum[u] = a ? __fadd_rn(sum[u], __uint_as_float(v[u]))
+                                   : __uint_as_float(v[u]);
+                }
+                const int gj0 = J * kTile + c0;
+                if (gi < n) {
+                    if (I != J && vec && gj0 + 16 <= n) {
+                        float4 *dst = reinterpret_cast<float4 *>(S + (long long)gi * ld + gj0);
 #pragma unroll
-                for (int q = 0; q < kTile / 32; ++q) {
-                    const int r = lane + 32 * q;
-                    const int gi = I * kTile + r;
-                    if (gi < n) S[(long long)gj * ld + gi] = tile[r * kLd + c];
+                        for (int u = 0; u < 4; ++u)
+                            dst[u] = make_float4(sum[4 * u], sum[4 * u + 1], sum[4 * u + 2],
+                                                 sum[4 * u + 3]);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) {
+                            const int gj = gj0 + u;
+                            if (gj < n && gj >= gi)
+                                S[(long long)gi * ld + gj] = gi == gj ? 1.0f : sum[u];
+                        }
+                    }
+                    // the transpose: S[gj, gi] for gj > gi (lanes write neighbours)
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int gj = gj0 + u;
+                        if (gj < n && gj > gi) S[(long long)gj * ld + gi] = sum[u];
+                    }
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(kAcc * kTile)
+                     "r"(2 * kBufCols)
                      : "memory");
 }
 
@@ -571,7 +602,15 @@ int launch_similarity(const float *X, int n, int T, long long ldx, int prec, flo
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem) !=
         cudaSuccess)
         return TMFG_ECUDA;
-    k<<<tiles, kTcThreads, kTcSmem, stream>>>(mh, ml, n, kblocks, S, ld, status, timeout_ns);
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // persistent: one CTA per SM (the pipeline's shared memory allows no
+    // second one, so the whole tensor memory is this CTA's)
+    const int grid = tiles < sms ? tiles : sms;
+    const bool vec = (ld % 4 == 0) && (reinterpret_cast<uintptr_t>(S) % 16 == 0);
+    k<<<grid, kTcThreads, kTcSmem, stream>>>(mh, ml, n, kblocks, tiles, S, ld, vec, status,
+                                             timeout_ns);
     return cudaGetLastError() == cudaSuccess ? TMFG_OK : TMFG_ECUDA;
 }
 

@@ -13,9 +13,9 @@ correlations.  The bound used (``tol``) is a worst case with three parts:
     step, T steps.  The tensor core accumulates in FP32 with truncation, so
     its errors can share a sign: <= 2 ulps (2^-22) per step, where a step is
     one MMA (K = 16 bf16 / 8 tf32 elements, 3 products per K slice) into one
-    of the 4 accumulators, whose partial sums add up to at most 1
-    (Cauchy-Schwarz over the K slices each one holds): ceil(steps / 4) steps;
-    the 4 accumulators are then added in FP32: 3 more roundings (2^-24).
+    of the 2 accumulators, whose partial sums add up to at most 1
+    (Cauchy-Schwarz over the K slices each one holds): ceil(steps / 2) steps;
+    the 2 accumulators are then added in FP32: one more rounding (2^-24).
 f64 keeps only the output rounding (1e-7).
 """
 import numpy as np
@@ -36,7 +36,7 @@ def tol(prec, Tlen):
         return 3 * 2.0 ** -24 + Tlen * 2.0 ** -24
     K, rep = (8, 2.0 ** -22) if prec == "tf32x3" else (16, 2.0 ** -18)
     steps = 3 * -(-Tlen // K)
-    return 3 * rep + -(-steps // 4) * 2.0 ** -22 + 4 * 2.0 ** -24
+    return 3 * rep + -(-steps // 2) * 2.0 ** -22 + 2 * 2.0 ** -24
 
 
 @pytest.fixture(scope="module")
@@ -100,6 +100,19 @@ def test_strided_tiles_and_many_tiles(T, ctx):
         S = run(T, ctx, X, prec)
         assert np.array_equal(S, S.T)
         assert np.abs(S - R).max() <= tol(prec, 300)
+
+
+def test_tiles_per_persistent_cta(T, ctx):
+    """More tiles than SMs: each persistent CTA runs several tiles, the
+    epilogue of one overlapping the accumulation of the next in the other
+    tensor-memory buffer."""
+    X = series(2500, 256, seed=29)
+    R = oracle.pearson(X)
+    for prec in ("bf16x3", "tf32x3"):
+        S = run(T, ctx, X, prec)
+        assert np.array_equal(S, S.T)
+        assert np.all(np.diag(S) == 1.0)
+        assert np.abs(S - R).max() <= tol(prec, 256)
 
 
 def test_constant_or_nonfinite_series_are_errors(T, ctx):

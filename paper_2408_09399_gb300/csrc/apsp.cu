@@ -119,11 +119,13 @@ __global__ void csr_fill_kernel(const int *__restrict__ edges, int ne, int n,
 // ----------------------------------------------------------------- SSSP
 
 // Shared memory: dist[n] floats, two frontier bitmaps, a frontier list of at
-// most list_cap ids, and a list of high-degree frontier vertices.
-// at least 32 entries, so that any one bitmap word fits an empty window
+// most list_cap ids, and a list of high-degree frontier vertices with their
+// arc ranges.  The list holds at least 32 entries, so that any one bitmap
+// word fits an empty window, and at most 8192.
 __host__ __device__ inline int sssp_list_cap(int n)
 {
-    return (((n / 2) > 32 ? (n / 2) : 32) + 15) & ~15;
+    const int c = (((n / 2) > 32 ? (n / 2) : 32) + 15) & ~15;
+    return c < 8192 ? c : 8192;
 }
 constexpr int kHeavyCap = 512;
 constexpr int kHeavyDeg = 16;
@@ -141,7 +143,8 @@ __device__ __forceinline__ bool sssp_source(const SsspArgs &a, int i, uint64_t t
     float *dist = reinterpret_cast<float *>(smem);
     uint32_t *bm0 = reinterpret_cast<uint32_t *>(smem + ((4 * (size_t)n + 15) & ~size_t(15)));
     uint32_t *bm1 = bm0 + W;
-    uint16_t *list = reinterpret_cast<uint16_t *>(bm1 + W);
+    int2 *hrange = reinterpret_cast<int2 *>(bm0 + 2 * W);  // 8-byte aligned
+    uint16_t *list = reinterpret_cast<uint16_t *>(hrange + kHeavyCap);
     uint16_t *heavy = list + cap;
     {
         if (tid == 0) s_abort = (*(volatile int *)a.status != 0) ||
@@ -198,35 +201,54 @@ __device__ __forceinline__ bool sssp_source(const SsspArgs &a, int i, uint64_t t
                     if (tid == 0) set_status(a.status, TMFG_EINTERNAL);
                     return false;
                 }
-                // relax: light vertices one per thread, heavy ones a warp each
-                for (int j = tid; j < cnt; j += NT) {
-                    const int u = list[j];
-                    if (u >= n) continue;
-                    const float du = dist[u];
-                    if (kBounded && du > r) continue;
-                    const int p0 = a.rowptr[u], p1 = a.rowptr[u + 1];
-                    if (p1 - p0 > kHeavyDeg) {
-                        const int h = atomicAdd(&s_hcnt, 1);
-                        if (h < kHeavyCap) {
-                            heavy[h] = (uint16_t)u;
-                            continue;
+                // relax: light vertices one per thread (two per pass, their
+                // loads issued together), heavy ones a warp each
+                auto relax = [&](float du, const uint2 &arc) {
+                    const int w = (int)arc.x;
+                    if (w < 0 || w >= n) return;
+                    const float nd = __fadd_rn(du, __uint_as_float(arc.y));
+                    if (nd < dist[w]) {
+                        const int old = atomicMin(reinterpret_cast<int *>(&dist[w]),
+                                                  __float_as_int(nd));
+                        if (__float_as_int(nd) < old) atomicOr(&nxt[w >> 5], 1u << (w & 31));
+                    }
+                };
+                for (int j = tid; j < cnt; j += 2 * NT) {
+                    int us[2], q0[2], q1[2];
+                    float du[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int jj = j + h * NT;
+                        us[h] = jj < cnt ? list[jj] : n;
+                        q0[h] = 0;
+                        q1[h] = 0;
+                        du[h] = 0.0f;
+                        if (us[h] < n) {
+                            du[h] = dist[us[h]];
+                            if (!(kBounded && du[h] > r)) {
+                                q0[h] = a.rowptr[us[h]];
+                                q1[h] = a.rowptr[us[h] + 1];
+                            }
                         }
                     }
-                    for (int p = p0; p < p1; p += 4) {
-                        uint2 arc[4];
 #pragma unroll
-                        for (int t = 0; t < 4; ++t)
-                            arc[t] = p + t < p1 ? a.arcs[p + t] : make_uint2(0xFFFFFFFFu, 0u);
-#pragma unroll
-                        for (int t = 0; t < 4; ++t) {
-                            const int w = (int)arc[t].x;
-                            if (w < 0 || w >= n) continue;
-                            const float nd = __fadd_rn(du, __uint_as_float(arc[t].y));
-                            if (nd < dist[w]) {
-                                const int old = atomicMin(reinterpret_cast<int *>(&dist[w]),
-                                                          __float_as_int(nd));
-                                if (__float_as_int(nd) < old) atomicOr(&nxt[w >> 5], 1u << (w & 31));
+                    for (int h = 0; h < 2; ++h) {
+                        const int p0 = q0[h], p1 = q1[h];
+                        if (p1 - p0 > kHeavyDeg) {
+                            const int hh = atomicAdd(&s_hcnt, 1);
+                            if (hh < kHeavyCap) {
+                                heavy[hh] = (uint16_t)us[h];
+                                hrange[hh] = make_int2(p0, p1);
+                                continue;
                             }
+                        }
+                        for (int p = p0; p < p1; p += 8) {
+                            uint2 arc[8];
+#pragma unroll
+                            for (int t = 0; t < 8; ++t)
+                                arc[t] = p + t < p1 ? a.arcs[p + t] : make_uint2(0xFFFFFFFFu, 0u);
+#pragma unroll
+                            for (int t = 0; t < 8; ++t) relax(du[h], arc[t]);
                         }
                     }
                 }
@@ -235,16 +257,15 @@ __device__ __forceinline__ bool sssp_source(const SsspArgs &a, int i, uint64_t t
                 for (int j = warp; j < hc; j += NT / 32) {
                     const int u = heavy[j];
                     const float du = dist[u];
-                    const int p1 = a.rowptr[u + 1];
-                    for (int p = a.rowptr[u] + lane; p < p1; p += 32) {
-                        const uint2 arc = a.arcs[p];
-                        const int w = (int)arc.x;
-                        const float nd = __fadd_rn(du, __uint_as_float(arc.y));
-                        if (nd < dist[w]) {
-                            const int old = atomicMin(reinterpret_cast<int *>(&dist[w]),
-                                                      __float_as_int(nd));
-                            if (__float_as_int(nd) < old) atomicOr(&nxt[w >> 5], 1u << (w & 31));
-                        }
+                    const int2 pr = hrange[j];
+                    for (int p = pr.x + lane; p < pr.y; p += 4 * 32) {
+                        uint2 arc[4];
+#pragma unroll
+                        for (int t = 0; t < 4; ++t)
+                            arc[t] = p + 32 * t < pr.y ? a.arcs[p + 32 * t]
+                                                      : make_uint2(0xFFFFFFFFu, 0u);
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) relax(du, arc[t]);
                     }
                 }
                 __syncthreads();
@@ -320,8 +341,8 @@ __global__ void __launch_bounds__(NT, 2) sssp_batch_kernel(const SsspArgs *__res
 size_t sssp_smem_bytes(int n)
 {
     const size_t W = (n + 31) / 32;
-    return ((4 * (size_t)n + 15) & ~size_t(15)) + 8 * W + 2 * (size_t)sssp_list_cap(n) +
-           2 * (size_t)kHeavyCap + 16;
+    return ((4 * (size_t)n + 15) & ~size_t(15)) + 8 * W + 8 * (size_t)kHeavyCap +
+           2 * (size_t)sssp_list_cap(n) + 2 * (size_t)kHeavyCap + 16;
 }
 
 // ------------------------------------------------------------- hubs

@@ -9,7 +9,8 @@
 //     (q = x*2^40 rounded to nearest-even, order independent) and checks that
 //     every off-diagonal entry is finite with |x| <= 64;
 //   * a stable LSD radix sort on 8-bit digits runs in shared memory; ranks
-//     inside a warp come from __match_any_sync, ranks across warps from a
+//     inside a warp come from eight ballots (one per digit bit: the lanes
+//     holding the same digit), ranks across warps from a
 //     block-wide scan of per-warp digit counts (digit-major), which keeps
 //     equal keys in ascending column order: (S desc, u asc);
 //   * for float rows the key shrinks by 8 bits per pass (32 -> 24 -> 16 -> 8
@@ -97,8 +98,15 @@ __device__ __forceinline__ void radix_pass(int m, uint32_t *hist, uint32_t *wsum
     for (int j = 0; j < I; ++j) {
         const int p = base + j * 32 + lane;
         const bool valid = p < m;
-        const uint32_t d = valid ? digit_of(p) : 0x100u + lane;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t d = valid ? digit_of(p) : 0u;
+        // lanes with the same digit: one ballot per digit bit
+        unsigned peers = __ballot_sync(0xffffffffu, valid);
+        peers = valid ? peers : (1u << lane);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const unsigned mb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? mb : ~mb;
+        }
         uint32_t before = valid ? h[d] : 0u;
         rank[j] = before + __popc(peers & lt);
         __syncwarp();

@@ -453,7 +453,7 @@ __device__ __forceinline__ unsigned long long lk_key(float d, int ra, int rb)
            (unsigned long long)r1;
 }
 
-// Best merge partner of row i (one warp).
+// Best merge partner of row i (one warp, four columns per lane in flight).
 __device__ __forceinline__ void lk_row_scan(int i, int m, const float *dm, const int *rep,
                                             const int *alive, unsigned long long *rowkey,
                                             int *rowbest, int lane)
@@ -462,10 +462,23 @@ __device__ __forceinline__ void lk_row_scan(int i, int m, const float *dm, const
     int bj = -1;
     const int ri = rep[i];
     const float *row = dm + (long long)i * m;
-    for (int j = lane; j < m; j += 32) {
-        if (j == i || !alive[j]) continue;
-        const unsigned long long k = lk_key(row[j], ri, rep[j]);
-        if (k < bk) { bk = k; bj = j; }
+    for (int j0 = lane; j0 < m; j0 += 4 * 32) {
+        float dv[4];
+        int rj[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 + 32 * u;
+            ok[u] = j < m && j != i && alive[j];
+            dv[u] = ok[u] ? row[j] : 0.0f;
+            rj[u] = ok[u] ? rep[j] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (ok[u]) {
+                const unsigned long long k = lk_key(dv[u], ri, rj[u]);
+                if (k < bk) { bk = k; bj = j0 + 32 * u; }
+            }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -479,23 +492,53 @@ __device__ __forceinline__ void lk_row_scan(int i, int m, const float *dm, const
     }
 }
 
+// Items whose per-item state (row key, best partner, alive flag,
+// representative, id, size: 28 bytes) the linkage keeps in shared memory.
+constexpr int kLkCap = 3072;
+constexpr size_t kLkSmem = 28 * (size_t)kLkCap;
+constexpr int kRB = 4;         // rows re-scanned together by the whole CTA
+constexpr int kLkUnroll = 4;   // columns per thread in flight during a re-scan
+constexpr int kLkUpd = 4;      // rows per thread in flight during a merge update
+constexpr int kLkMaxWarps = kDbThreads / 32;
+
 // Complete linkage of m >= 2 items by one CTA.  dm: m x m distances in
 // global memory (destroyed); id/rep/sz per item.  Each merge takes the
-// smallest key over all pairs.  The row minima stay current: a row whose
-// partner merged is re-scanned by a warp, every other row compares with the
-// merged cluster only (its distance can only grow, but its representative
-// can shrink).  Merge `step` writes linkage row row0 + step and leaves the
-// merged cluster in the lower slot; the final cluster goes to out_*.
-__device__ void linkage_cta(int m, float *dm, int *id, int *rep, int *sz,
-                            unsigned long long *rowkey, int *rowbest, int *alive, int n, int row0,
-                            double *Z, int *status, int *out_id, int *out_rep, int *out_sz)
+// smallest key over all pairs (keys are unique per pair: they carry both
+// representatives).  The row minima stay current: after a merge (a, b), one
+// pass over the other rows writes row and column a as the maxima of rows a
+// and b and updates each row's minimum with its new distance to a; rows
+// whose partner was a or b, and row a, are re-scanned by the whole CTA.
+// Merge `step` writes linkage row row0 + step and leaves the merged cluster
+// in the lower slot; the final cluster goes to out_*.  With m <= cap the
+// per-item state lives in `sm` (cap * 28 bytes of shared memory).
+__device__ void linkage_cta(int m, float *dm, int *id_g, int *rep_g, int *sz_g,
+                            unsigned long long *rowkey_g, int *rowbest_g, int *alive_g, int n,
+                            int row0, double *Z, int *status, int *out_id, int *out_rep,
+                            int *out_sz, unsigned char *sm, int cap)
 {
     __shared__ unsigned long long s_k[32];
     __shared__ int s_i[32];
     __shared__ int s_a, s_b, s_nres, s_fail;
     __shared__ int s_res[kResCap];
+    __shared__ unsigned long long s_pk[kRB * kLkMaxWarps];
+    __shared__ int s_pj[kRB * kLkMaxWarps];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
-    for (int i = t; i < m; i += blockDim.x) alive[i] = 1;
+    const bool fits = m <= cap;
+    unsigned long long *rowkey =
+        fits ? reinterpret_cast<unsigned long long *>(sm) : rowkey_g;
+    int *rowbest = fits ? reinterpret_cast<int *>(sm + 8 * (size_t)cap) : rowbest_g;
+    int *alive = fits ? reinterpret_cast<int *>(sm + 12 * (size_t)cap) : alive_g;
+    int *rep = fits ? reinterpret_cast<int *>(sm + 16 * (size_t)cap) : rep_g;
+    int *id = fits ? reinterpret_cast<int *>(sm + 20 * (size_t)cap) : id_g;
+    int *sz = fits ? reinterpret_cast<int *>(sm + 24 * (size_t)cap) : sz_g;
+    for (int i = t; i < m; i += blockDim.x) {
+        alive[i] = 1;
+        if (fits) {
+            rep[i] = rep_g[i];
+            id[i] = id_g[i];
+            sz[i] = sz_g[i];
+        }
+    }
     if (t == 0) s_fail = 0;
     __syncthreads();
     for (int i = warp; i < m; i += nw) lk_row_scan(i, m, dm, rep, alive, rowkey, rowbest, lane);
@@ -533,7 +576,8 @@ __device__ void linkage_cta(int m, float *dm, int *id, int *rep, int *sz,
                 const int ia = id[a], ib = id[b];
                 Z[4 * row + 0] = (double)(ia < ib ? ia : ib);
                 Z[4 * row + 1] = (double)(ia < ib ? ib : ia);
-                Z[4 * row + 2] = (double)dm[(long long)a * m + b];
+                // the key carries the pair's distance bits (dm[a][b])
+                Z[4 * row + 2] = (double)__uint_as_float((unsigned)(k >> 30));
                 Z[4 * row + 3] = (double)(sz[a] + sz[b]);
                 id[a] = n + row;
                 rep[a] = rep[a] < rep[b] ? rep[a] : rep[b];
@@ -544,43 +588,123 @@ __device__ void linkage_cta(int m, float *dm, int *id, int *rep, int *sz,
         }
         __syncthreads();
         if (s_fail) break;
-        const int a = s_a, b = s_b;
-        for (int k = t; k < m; k += blockDim.x) {
-            if (!alive[k] || k == a) continue;
-            const float d1 = dm[(long long)a * m + k], d2 = dm[(long long)b * m + k];
-            const float d = d1 > d2 ? d1 : d2;
-            dm[(long long)a * m + k] = d;
-            dm[(long long)k * m + a] = d;
-        }
-        __syncthreads();
-        for (int k = t; k < m; k += blockDim.x) {
-            if (!alive[k]) continue;
-            if (k == a || rowbest[k] == a || rowbest[k] == b) {
-                const int slot = atomicAdd(&s_nres, 1);
-                if (slot < kResCap) {
-                    s_res[slot] = k;
-                } else {  // list full: this thread scans the row itself
-                    unsigned long long bk2 = ~0ull;
-                    int bj2 = -1;
-                    for (int j = 0; j < m; ++j) {
-                        if (j == k || !alive[j]) continue;
-                        const unsigned long long kk =
-                            lk_key(dm[(long long)k * m + j], rep[k], rep[j]);
-                        if (kk < bk2) { bk2 = kk; bj2 = j; }
+        const int a = s_a, b = s_b, repa = rep[a];
+        // row and column a = max of rows a and b; minima of the other rows
+        // (kLkUpd rows per thread with their loads in flight)
+        for (int k0 = t; k0 < m; k0 += kLkUpd * blockDim.x) {
+            float d1[kLkUpd], d2[kLkUpd];
+            bool live[kLkUpd];
+#pragma unroll
+            for (int u = 0; u < kLkUpd; ++u) {
+                const int k = k0 + u * blockDim.x;
+                live[u] = k < m && alive[k];
+                const bool ld = live[u] && k != a;
+                d1[u] = ld ? dm[(long long)a * m + k] : 0.0f;
+                d2[u] = ld ? dm[(long long)b * m + k] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < kLkUpd; ++u) {
+                const int k = k0 + u * blockDim.x;
+                if (!live[u]) continue;
+                bool again = k == a;
+                if (!again) {
+                    const float d = d1[u] > d2[u] ? d1[u] : d2[u];
+                    dm[(long long)a * m + k] = d;
+                    dm[(long long)k * m + a] = d;
+                    const int pb = rowbest[k];
+                    again = pb == a || pb == b;
+                    if (!again) {
+                        const unsigned long long kk = lk_key(d, rep[k], repa);
+                        if (kk < rowkey[k]) { rowkey[k] = kk; rowbest[k] = a; }
                     }
-                    rowkey[k] = bk2;
-                    rowbest[k] = bj2;
                 }
-            } else {
-                const unsigned long long kk = lk_key(dm[(long long)k * m + a], rep[k], rep[a]);
-                if (kk < rowkey[k]) { rowkey[k] = kk; rowbest[k] = a; }
+                if (again) {
+                    const int slot = atomicAdd(&s_nres, 1);
+                    if (slot < kResCap) s_res[slot] = k;
+                    else rowbest[k] = -2;  // re-scanned by this thread below
+                }
             }
         }
         __syncthreads();
+        // rows beyond the list (more than kResCap re-scans in one merge)
+        if (s_nres > kResCap)
+            for (int k = t; k < m; k += blockDim.x) {
+                if (!alive[k] || rowbest[k] != -2) continue;
+                unsigned long long bk2 = ~0ull;
+                int bj2 = -1;
+                for (int j = 0; j < m; ++j) {
+                    if (j == k || !alive[j]) continue;
+                    const unsigned long long kk = lk_key(dm[(long long)k * m + j], rep[k], rep[j]);
+                    if (kk < bk2) { bk2 = kk; bj2 = j; }
+                }
+                rowkey[k] = bk2;
+                rowbest[k] = bj2;
+            }
+        // the listed rows, kRB at a time, by the whole CTA
         const int nres = min(s_nres, kResCap);
-        for (int r = warp; r < nres; r += nw)
-            lk_row_scan(s_res[r], m, dm, rep, alive, rowkey, rowbest, lane);
-        __syncthreads();
+        for (int r0 = 0; r0 < nres; r0 += kRB) {
+            int ri[kRB], rr[kRB];
+            unsigned long long bq[kRB];
+            int bjq[kRB];
+#pragma unroll
+            for (int q = 0; q < kRB; ++q) {
+                ri[q] = r0 + q < nres ? s_res[r0 + q] : -1;
+                rr[q] = ri[q] >= 0 ? rep[ri[q]] : 0;
+                bq[q] = ~0ull;
+                bjq[q] = -1;
+            }
+            for (int j0 = t; j0 < m; j0 += kLkUnroll * blockDim.x) {
+                float dv[kLkUnroll][kRB];
+                int rj[kLkUnroll];
+                bool ok[kLkUnroll];
+#pragma unroll
+                for (int u = 0; u < kLkUnroll; ++u) {
+                    const int j = j0 + u * blockDim.x;
+                    ok[u] = j < m && alive[j];
+                    rj[u] = ok[u] ? rep[j] : 0;
+#pragma unroll
+                    for (int q = 0; q < kRB; ++q)
+                        dv[u][q] = (ok[u] && ri[q] >= 0 && ri[q] != j) ? dm[(long long)ri[q] * m + j]
+                                                                       : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < kLkUnroll; ++u) {
+                    const int j = j0 + u * blockDim.x;
+#pragma unroll
+                    for (int q = 0; q < kRB; ++q)
+                        if (ok[u] && ri[q] >= 0 && ri[q] != j) {
+                            const unsigned long long kk = lk_key(dv[u][q], rr[q], rj[u]);
+                            if (kk < bq[q]) { bq[q] = kk; bjq[q] = j; }
+                        }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kRB; ++q) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, bq[q], o);
+                    const int j2 = __shfl_xor_sync(0xffffffffu, bjq[q], o);
+                    if (k2 < bq[q]) { bq[q] = k2; bjq[q] = j2; }
+                }
+                if (lane == 0) {
+                    s_pk[q * kLkMaxWarps + warp] = bq[q];
+                    s_pj[q * kLkMaxWarps + warp] = bjq[q];
+                }
+            }
+            __syncthreads();
+            if (t < kRB && r0 + t < nres) {
+                unsigned long long k = s_pk[t * kLkMaxWarps];
+                int j = s_pj[t * kLkMaxWarps];
+                for (int q = 1; q < nw; ++q)
+                    if (s_pk[t * kLkMaxWarps + q] < k) {
+                        k = s_pk[t * kLkMaxWarps + q];
+                        j = s_pj[t * kLkMaxWarps + q];
+                    }
+                rowkey[s_res[r0 + t]] = k;
+                rowbest[s_res[r0 + t]] = j;
+            }
+            __syncthreads();
+        }
     }
     if (t == 0) {
         for (int i = 0; i < m; ++i)
@@ -618,7 +742,7 @@ __global__ void __launch_bounds__(kDbThreads) dbht_l1_kernel(DbWork w, const flo
         }
         __syncthreads();
         linkage_cta(m, dm, id, rep, sz, w.rowkey + beg, w.rowbest + beg, w.alive + beg, w.n,
-                    w.l1_off[b], Z, w.status, &w.cid[b], &w.crep[b], &w.csz[b]);
+                    w.l1_off[b], Z, w.status, &w.cid[b], &w.crep[b], &w.csz[b], nullptr, 0);
     }
 }
 
@@ -694,6 +818,7 @@ __device__ void symmetrize_max(float *dm, int m)
 // level 2: complete linkage of the cells of each group (one CTA per group)
 __global__ void __launch_bounds__(kDbThreads) dbht_l2_kernel(DbWork w, double *Z)
 {
+    extern __shared__ __align__(16) unsigned char lk_smem[];
     if (*w.status) return;
     const int nc = w.scal[0];
     for (int c = blockIdx.x; c < nc; c += gridDim.x) {
@@ -718,13 +843,14 @@ __global__ void __launch_bounds__(kDbThreads) dbht_l2_kernel(DbWork w, double *Z
         }
         symmetrize_max(dm, m);
         linkage_cta(m, dm, id, rep, sz, w.rowkey + beg, w.rowbest + beg, w.alive + beg, w.n,
-                    w.l2_off[c], Z, w.status, &w.gid[c], &w.grep[c], &w.gsz[c]);
+                    w.l2_off[c], Z, w.status, &w.gid[c], &w.grep[c], &w.gsz[c], lk_smem, kLkCap);
     }
 }
 
 // level 3: complete linkage of the groups (one CTA)
 __global__ void __launch_bounds__(kDbThreads) dbht_l3_kernel(DbWork w, double *Z)
 {
+    extern __shared__ __align__(16) unsigned char lk_smem[];
     if (*w.status) return;
     __shared__ int s_id, s_rep, s_sz;
     const int nc = w.scal[0], ng = w.scal[3];
@@ -740,7 +866,8 @@ __global__ void __launch_bounds__(kDbThreads) dbht_l3_kernel(DbWork w, double *Z
     symmetrize_max(dm, ng);
     if (ng >= 2)
         linkage_cta(ng, dm, w.items_id, w.items_rep, w.items_sz, w.rowkey, w.rowbest, w.alive,
-                    w.n, w.scal[1] + w.scal[2], Z, w.status, &s_id, &s_rep, &s_sz);
+                    w.n, w.scal[1] + w.scal[2], Z, w.status, &s_id, &s_rep, &s_sz, lk_smem,
+                    kLkCap);
 }
 
 // optional per-vertex / per-bubble outputs
@@ -893,8 +1020,13 @@ int launch_dbht(const void *S, int n, long long ld, int dtype, const int *order,
     dbht_zero_kernel<<<g, 256, 0, stream>>>(w);
     dbht_l1_kernel<<<g, kDbThreads, 0, stream>>>(w, D, ldd, Z);
     dbht_dist_kernel<<<8 * num_sms, 256, 0, stream>>>(w, D, ldd);
-    dbht_l2_kernel<<<g, kDbThreads, 0, stream>>>(w, Z);
-    dbht_l3_kernel<<<1, kDbThreads, 0, stream>>>(w, Z);
+    if (cudaFuncSetAttribute(dbht_l2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kLkSmem) != cudaSuccess ||
+        cudaFuncSetAttribute(dbht_l3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kLkSmem) != cudaSuccess)
+        return TMFG_ECUDA;
+    dbht_l2_kernel<<<g, kDbThreads, kLkSmem, stream>>>(w, Z);
+    dbht_l3_kernel<<<1, kDbThreads, kLkSmem, stream>>>(w, Z);
     if (direction || converging || group || bubble)
         dbht_extra_kernel<<<g, 256, 0, stream>>>(w, direction, converging, group, bubble);
     return cudaGetLastError() == cudaSuccess ? TMFG_OK : TMFG_ECUDA;

@@ -713,6 +713,197 @@ __device__ void linkage_cta(int m, float *dm, int *id_g, int *rep_g, int *sz_g,
     __syncthreads();
 }
 
+// Complete linkage by the nearest-neighbour chain (one CTA, 2 <= m <=
+// kChainMax items, state in `sm`).  Complete linkage is reducible --
+// d(i+j, k) = max(d(i,k), d(j,k)) >= min(d(i,k), d(j,k)) -- and the keys
+// order all pairs strictly (with equal distances the merged cluster's key to
+// k equals one of its parts' keys, since its representative is the smaller
+// of the two), so merging reciprocal nearest neighbours as the chain finds
+// them builds the same hierarchy as always merging the globally smallest
+// key, and the merge keys of that sequential order increase strictly.  The
+// merges are therefore recorded with their keys, sorted, and replayed in
+// key order to write the linkage rows and cluster ids exactly as the
+// sequential order does.  Each chain step is one row scan by the whole CTA
+// (no row minima to keep current), a merge one more pass over rows a and b.
+constexpr int kChainMax = 2048;
+constexpr int kChainUnroll = 8;   // row entries per thread in flight (m <= 2048)
+__device__ void linkage_chain_cta(int m, float *dm, const int *id_g, const int *rep_g,
+                                  const int *sz_g, int n, int row0, double *Z, int *status,
+                                  int *out_id, int *out_rep, int *out_sz, unsigned char *sm)
+{
+    __shared__ unsigned long long s_pk[kLkMaxWarps];
+    __shared__ int s_pj[kLkMaxWarps];
+    __shared__ int s_x, s_len, s_merges, s_start, s_act, s_a, s_b, s_fail;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+    unsigned long long *mkey = reinterpret_cast<unsigned long long *>(sm);
+    int *mab = reinterpret_cast<int *>(sm + 8 * (size_t)kChainMax);
+    int *chain = mab + kChainMax;
+    int *alive = chain + kChainMax;
+    int *rep = alive + kChainMax;
+    int *id = rep + kChainMax;
+    int *sz = id + kChainMax;
+    for (int i = t; i < m; i += blockDim.x) {
+        alive[i] = 1;
+        rep[i] = rep_g[i];
+        id[i] = id_g[i];
+        sz[i] = sz_g[i];
+    }
+    if (t == 0) {
+        s_len = 1;
+        chain[0] = 0;
+        s_x = 0;
+        s_merges = 0;
+        s_start = 0;
+        s_fail = 0;
+    }
+    __syncthreads();
+    const int nmerge = m - 1;
+    // at most 2m - 1 pushes and m - 1 merges
+    for (int iter = 0; s_merges < nmerge; ++iter) {
+        if (iter > 3 * m) {
+            if (t == 0) set_status(status, TMFG_EINTERNAL);
+            return;
+        }
+        // nearest neighbour of the chain's top x
+        const int x = s_x, rx = rep[x];
+        const float *row = dm + (long long)x * m;
+        unsigned long long bk = ~0ull;
+        int bj = -1;
+        for (int j0 = t; j0 < m; j0 += kChainUnroll * blockDim.x) {
+            float dv[kChainUnroll];
+            int rj[kChainUnroll];
+            bool ok[kChainUnroll];
+#pragma unroll
+            for (int u = 0; u < kChainUnroll; ++u) {
+                const int j = j0 + u * blockDim.x;
+                ok[u] = j < m && j != x && alive[j];
+                dv[u] = ok[u] ? row[j] : 0.0f;
+                rj[u] = ok[u] ? rep[j] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < kChainUnroll; ++u)
+                if (ok[u]) {
+                    const unsigned long long k = lk_key(dv[u], rx, rj[u]);
+                    if (k < bk) { bk = k; bj = j0 + u * blockDim.x; }
+                }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, bk, o);
+            const int j2 = __shfl_xor_sync(0xffffffffu, bj, o);
+            if (k2 < bk) { bk = k2; bj = j2; }
+        }
+        if (lane == 0) { s_pk[warp] = bk; s_pj[warp] = bj; }
+        __syncthreads();
+        if (t == 0) {
+            unsigned long long k = s_pk[0];
+            int y = s_pj[0];
+            for (int q = 1; q < nw; ++q)
+                if (s_pk[q] < k) { k = s_pk[q]; y = s_pj[q]; }
+            s_act = 0;
+            if (y < 0) {
+                s_fail = 1;
+                set_status(status, TMFG_EINTERNAL);
+            } else if (s_len >= 2 && chain[s_len - 2] == y) {
+                // reciprocal nearest neighbours: merge into the lower slot
+                const int a = x < y ? x : y, b = x < y ? y : x;
+                mkey[s_merges] = k;
+                mab[s_merges] = a | (b << 16);
+                ++s_merges;
+                rep[a] = rep[a] < rep[b] ? rep[a] : rep[b];
+                alive[b] = 0;
+                s_len -= 2;
+                s_a = a;
+                s_b = b;
+                s_act = 1;
+                if (s_len == 0) {  // restart the chain at the smallest live item
+                    while (s_start < m && !alive[s_start]) ++s_start;
+                    chain[s_len++] = s_start < m ? s_start : a;
+                }
+                s_x = chain[s_len - 1];
+            } else if (s_len >= m) {  // a chain longer than the items: cannot happen
+                s_fail = 1;
+                set_status(status, TMFG_EINTERNAL);
+            } else {
+                chain[s_len++] = y;
+                s_x = y;
+            }
+        }
+        __syncthreads();
+        if (s_fail) return;
+        if (s_act) {
+            // row and column a = max of rows a and b
+            const int a = s_a, b = s_b;
+            for (int k0 = t; k0 < m; k0 += kChainUnroll * blockDim.x) {
+                float d1[kChainUnroll], d2[kChainUnroll];
+                bool ok[kChainUnroll];
+#pragma unroll
+                for (int u = 0; u < kChainUnroll; ++u) {
+                    const int k = k0 + u * blockDim.x;
+                    ok[u] = k < m && k != a && alive[k];
+                    d1[u] = ok[u] ? dm[(long long)a * m + k] : 0.0f;
+                    d2[u] = ok[u] ? dm[(long long)b * m + k] : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < kChainUnroll; ++u)
+                    if (ok[u]) {
+                        const int k = k0 + u * blockDim.x;
+                        const float d = d1[u] > d2[u] ? d1[u] : d2[u];
+                        dm[(long long)a * m + k] = d;
+                        dm[(long long)k * m + a] = d;
+                    }
+            }
+            __syncthreads();
+        }
+    }
+    // the merges in key order (bitonic sort of the key / pair records)
+    int P = 1;
+    while (P < nmerge) P <<= 1;
+    for (int i = nmerge + t; i < P; i += blockDim.x) {
+        mkey[i] = ~0ull;
+        mab[i] = 0;
+    }
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = t; i < P; i += blockDim.x) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool up = (i & size) == 0;
+                    const unsigned long long ki = mkey[i], kj = mkey[j];
+                    if ((ki > kj) == up) {
+                        mkey[i] = kj;
+                        mkey[j] = ki;
+                        const int tmp = mab[i];
+                        mab[i] = mab[j];
+                        mab[j] = tmp;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    // replay: linkage rows and cluster ids in the sequential order
+    if (t == 0) {
+        int last = 0;
+        for (int r = 0; r < nmerge; ++r) {
+            const int a = mab[r] & 0xFFFF, b = (mab[r] >> 16) & 0xFFFF;
+            const int row = row0 + r;
+            const int ia = id[a], ib = id[b];
+            Z[4 * row + 0] = (double)(ia < ib ? ia : ib);
+            Z[4 * row + 1] = (double)(ia < ib ? ib : ia);
+            Z[4 * row + 2] = (double)__uint_as_float((unsigned)(mkey[r] >> 30));
+            Z[4 * row + 3] = (double)(sz[a] + sz[b]);
+            id[a] = n + row;
+            sz[a] += sz[b];
+            last = a;
+        }
+        *out_id = id[last];
+        *out_rep = rep[last];
+        *out_sz = sz[last];
+    }
+    __syncthreads();
+}
+
 // level 1: complete linkage inside each cell (one CTA per cell)
 __global__ void __launch_bounds__(kDbThreads) dbht_l1_kernel(DbWork w, const float *D,
                                                              long long ldd, double *Z)
@@ -842,8 +1033,13 @@ __global__ void __launch_bounds__(kDbThreads) dbht_l2_kernel(DbWork w, double *Z
             sz[i] = w.csz[b];
         }
         symmetrize_max(dm, m);
-        linkage_cta(m, dm, id, rep, sz, w.rowkey + beg, w.rowbest + beg, w.alive + beg, w.n,
-                    w.l2_off[c], Z, w.status, &w.gid[c], &w.grep[c], &w.gsz[c], lk_smem, kLkCap);
+        if (m <= kChainMax)
+            linkage_chain_cta(m, dm, id, rep, sz, w.n, w.l2_off[c], Z, w.status, &w.gid[c],
+                              &w.grep[c], &w.gsz[c], lk_smem);
+        else
+            linkage_cta(m, dm, id, rep, sz, w.rowkey + beg, w.rowbest + beg, w.alive + beg, w.n,
+                        w.l2_off[c], Z, w.status, &w.gid[c], &w.grep[c], &w.gsz[c], lk_smem,
+                        kLkCap);
     }
 }
 
@@ -864,7 +1060,10 @@ __global__ void __launch_bounds__(kDbThreads) dbht_l3_kernel(DbWork w, double *Z
         }
     }
     symmetrize_max(dm, ng);
-    if (ng >= 2)
+    if (ng >= 2 && ng <= kChainMax)
+        linkage_chain_cta(ng, dm, w.items_id, w.items_rep, w.items_sz, w.n,
+                          w.scal[1] + w.scal[2], Z, w.status, &s_id, &s_rep, &s_sz, lk_smem);
+    else if (ng >= 2)
         linkage_cta(ng, dm, w.items_id, w.items_rep, w.items_sz, w.rowkey, w.rowbest, w.alive,
                     w.n, w.scal[1] + w.scal[2], Z, w.status, &s_id, &s_rep, &s_sz, lk_smem,
                     kLkCap);

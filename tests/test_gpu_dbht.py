@@ -96,6 +96,19 @@ def test_dbht_config2_shapes(T, ctx, n):
     assert_matches_oracle(S, th, D, Z, info, f"n={n}")
 
 
+def test_dbht_ties_in_large_groups(T, ctx):
+    """Planted clusters with S rounded to multiples of 1/16: groups of
+    hundreds of cells whose distances tie often, so the merge order of the
+    nearest-neighbour chain rests on the representative tie-break; the
+    dendrogram must still be the oracle's sequential smallest-key one."""
+    S, _ = W.config_similarity(2, n=1500)
+    S = (np.round(np.asarray(S, np.float64) * 16.0) / 16.0).astype(np.float32)
+    th, D, Z, info = gpu_pipeline(T, ctx, S)
+    check_linkage(Z, S.shape[0])
+    assert len(np.unique(Z[:, 2])) < len(Z) // 2  # many tied merge heights
+    assert_matches_oracle(S, th, D, Z, info, "quantized n=1500")
+
+
 def test_dbht_planted_clusters_recovered(T, ctx):
     """Section 5: on clean planted inputs the cut at the true k recovers the
     clusters exactly (ARI = 1), from the device dendrogram."""

@@ -423,6 +423,21 @@ def run_ours(args, rank, world, local):
                 "other_kernels": {"rowsort": line(6.0 * n * n, sort_ms),
                                   "apsp_exact": line(4.0 * n * n, apsp_ms),
                                   "apsp_approx": line(4.0 * n * n, apsx_ms)}}
+    # the loop's own bound: each insertion is a chain of dependent round
+    # trips -- the updated faces' records (L2) -> the probes of the sorted
+    # rows whose best vertex was inserted (DRAM) -> the gathers of S for the
+    # re-evaluated faces (DRAM) -> the reload of the touched index leaves
+    # (L2) -> the next root.  Latencies measured here by pointer chasing.
+    if rank == 0:
+        l2_ns = T.tmfg_memory_latency(ctx, 16 << 20, hops=20000, warm=(16 << 20) // 128)
+        dram_ns = T.tmfg_memory_latency(ctx, 4 << 30, hops=20000)
+        ins_ns = stats["loop_ns"] / max(n - 4, 1)
+        floor_ns = 2.0 * l2_ns + 2.0 * dram_ns
+        roofline["latency"] = {"l2_hit_ns": round(l2_ns, 1), "dram_miss_ns": round(dram_ns, 1),
+                               "chain": "2 L2 + 2 DRAM dependent round trips per insertion",
+                               "floor_ns_per_insertion": round(floor_ns, 1),
+                               "achieved_ns_per_insertion": round(ins_ns, 1),
+                               "frac": round(floor_ns / ins_ns, 4)}
 
     # e2e: the same step through the host-memory entry point (tmfg_solve_host):
     # S from page-locked host memory, the TMFG and both distance matrices

@@ -386,6 +386,20 @@ int tmfg_sync_status(tmfg_ctx *ctx, void *stream);
  * written. */
 int tmfg_last_stats(tmfg_ctx *ctx, int64_t *out, int count);
 
+/* Latency of dependent device-memory loads (no counterpart in the paper: a
+ * diagnostic for the insertion loop, whose bound is a chain of dependent
+ * round trips).  Allocates a buffer of `bytes` (rounded down to a power of
+ * two of 128-byte lines, at least 4096 bytes), links its lines into one
+ * scattered full-period cycle, follows `warm` links untimed and then `hops`
+ * links timed by the device clock, one thread with L1-bypassing loads, and
+ * frees the buffer.  A buffer well inside L2 after a warm pass of one period
+ * gives the L2 hit latency; a multi-gigabyte buffer, cold, gives the DRAM
+ * miss latency with its address-translation misses.  Synchronous (legacy
+ * default stream).  *ns_per_hop: host double.  Returns TMFG_EINVAL,
+ * TMFG_ENOMEM (the buffer does not fit) or TMFG_ECUDA on failure. */
+int tmfg_memory_latency(tmfg_ctx *ctx, int64_t bytes, int32_t hops, int32_t warm,
+                        double *ns_per_hop);
+
 /* Static description of a return code. */
 const char *tmfg_strerror(int code);
 

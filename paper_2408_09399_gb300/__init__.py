@@ -136,6 +136,8 @@ def load_library():
         lib.tmfg_sync_status.restype = ctypes.c_int
         lib.tmfg_last_stats.argtypes = [P, P, ctypes.c_int]
         lib.tmfg_last_stats.restype = ctypes.c_int
+        lib.tmfg_memory_latency.argtypes = [P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P]
+        lib.tmfg_memory_latency.restype = ctypes.c_int
         lib.tmfg_strerror.argtypes = [ctypes.c_int]
         lib.tmfg_strerror.restype = ctypes.c_char_p
         _lib = lib
@@ -562,6 +564,17 @@ def tmfg_last_stats(ctx: Context) -> dict:
             "cycles_extract", "cycles_validate", "cycles_resolve", "cycles_stale_scan",
             "epoch_iters"]
     return {k: int(arr[i]) for i, k in enumerate(keys)}
+
+
+def tmfg_memory_latency(ctx: Context, nbytes: int, hops: int = 20000, warm: int = 0) -> float:
+    """Nanoseconds per dependent load over a scattered cycle of 128-byte
+    lines in a fresh buffer of ``nbytes`` (see tmfg_memory_latency in
+    include/tmfg.h): a buffer inside L2 with ``warm`` = its line count gives
+    the L2 hit latency, a cold multi-gigabyte one the DRAM miss latency."""
+    ns = ctypes.c_double()
+    _check(load_library().tmfg_memory_latency(ctx.handle, int(nbytes), int(hops), int(warm),
+                                              ctypes.byref(ns)), "tmfg_memory_latency")
+    return ns.value
 
 
 def tmfg_strerror(code: int) -> str:

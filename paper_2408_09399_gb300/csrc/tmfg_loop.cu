@@ -17,11 +17,12 @@
 // recomputes the marked groups (a warp per group) and the root.
 //
 // MaxCorrs[w] is read fresh: the cached Mc[w] is kept while uninserted, else
-// the lazily advanced pointer of Section 4.3 moves on -- first one thread
-// probes the next 64 sorted ids (eight 16-byte loads in flight, the 64
-// inserted-bitmap checks independent of one another), and only rows whose
-// probe finds nothing go to a warp that scans 256 sorted ids per step with
-// 16-byte loads and a ballot.  A face's best
+// the lazily advanced pointer of Section 4.3 moves on -- first the next 64
+// sorted ids are probed (corr-tmfg: by a group of 8 lanes, one 16-byte load
+// and 8 inserted-bitmap checks each, the rows to probe listed while the
+// update's vertices are gathered; heap-tmfg: by one thread, eight 16-byte
+// loads), and only rows whose probe finds nothing go to a warp that scans
+// 256 sorted ids per step with 16-byte loads and a ballot.  A face's best
 // vertex is computed by one thread: 9 independent gathers S[x,u] (3
 // candidates u x 3 face vertices x), gain = (S[a,u] + S[b,u]) + S[c,u] with
 // round-to-nearest adds in the dtype of S, ties to the smaller u.
@@ -158,7 +159,7 @@ struct Tree {
 // Shared-memory layout (dynamic part), computed identically on the host.
 struct LoopLayout {
     int W, nfmax, G1, G2;
-    size_t off_ins, off_vmark, off_rnd, off_mc, off_ptr, off_fv, off_tree[2], off_vlist, off_vslow,
+    size_t off_ins, off_vmark, off_rnd, off_mc, off_ptr, off_fv, off_tree[2], off_vlist, off_vslow, off_plist,
         off_sel, off_x, off_xkey, off_xpend, off_xs, off_q1x, off_q2x, off_fus, total;
     size_t tree_bytes;
 };
@@ -197,6 +198,9 @@ __host__ __device__ inline LoopLayout loop_layout(int n, size_t ks, int ntrees)
     L.off_tree[1] = o; o += ntrees > 1 ? L.tree_bytes : 0;
     L.off_vlist = o; o = align16(o + 4 * (size_t)(3 * kChunk));
     L.off_vslow = o; o = align16(o + 4 * (size_t)(3 * kChunk));
+    // the list of rows to probe by 8-lane groups: corr-tmfg only (heap mode
+    // probes one row per thread and keeps its shared memory for two indexes)
+    L.off_plist = o; o = align16(o + (ntrees > 1 ? 0 : 4 * (size_t)(3 * kChunk)));
     L.off_sel = o;   o = align16(o + ks * (size_t)kMaxPrefix);
     // the stale-pop resolution arrays exist in heap mode (two indexes) only
     const size_t hx = ntrees > 1 ? 1 : 0;
@@ -248,7 +252,8 @@ struct Loop {
     uint32_t *ins, *vmark, *rnd;
     uint16_t *mc, *ptr, *fv;
     Tree<KO> tf, ts;  // FRESH (all faces in corr mode), STALE (heap mode)
-    int *vlist, *vslowlist;
+    int *vlist, *vslowlist, *plist;
+    int *pcount;
     Key *sel, *xkey, *xpend;
     int *xf;
     uint16_t *xs, *q1x, *q2x;
@@ -355,9 +360,9 @@ struct Loop {
         __syncwarp();
     }
 
-    // One thread's first look for the fresh MaxCorrs of w: the 16 sorted ids
-    // after ptr[w] (two 16-byte loads).  Returns false if w still needs the
-    // warp-wide scan.
+    // One thread's first look for the fresh MaxCorrs of w: the 64 sorted ids
+    // from ptr[w] + 1 rounded down to 8 (eight 16-byte loads).  Returns false
+    // if w still needs the warp-wide scan.
     __device__ bool refresh_probe(int w)
     {
         const uint16_t m = mc[w];
@@ -404,6 +409,67 @@ struct Loop {
             return true;
         }
         ptr[w] = (uint16_t)(base + 63);  // all 64 inserted (so base + 63 < mlen)
+        return false;
+    }
+
+    // The first look for row w by an 8-lane group (lanes 8g..8g+7 of a warp,
+    // sl = lane & 7): each lane loads 8 sorted ids (16 bytes), the group's
+    // first candidate wins.  Same outcome as refresh_probe.  Returns false
+    // (to every lane of the group) if w still needs the warp-wide scan.
+    __device__ bool refresh_probe8(int w)
+    {
+        const int lane = threadIdx.x & 31, sl = lane & 7, g0 = lane & ~7;
+        const unsigned gmask = 0xFFu << g0;
+        const int mlen = n - 1;
+        const int p = ptr[w] + 1;
+        if (p >= mlen) {
+            __syncwarp(gmask);
+            if (sl == 0) { ptr[w] = (uint16_t)mlen; mc[w] = kNone16; }
+            return true;
+        }
+        const uint16_t *row = a.idx + (long long)w * a.ldi;
+        const int base = p & ~7;
+        const int q0 = base + 8 * sl;
+        uint16_t e[8] = {kNone16, kNone16, kNone16, kNone16, kNone16, kNone16, kNone16, kNone16};
+        if (q0 < a.ldi) {
+            const uint4 c = *reinterpret_cast<const uint4 *>(row + q0);
+            e[0] = c.x & 0xFFFF; e[1] = c.x >> 16; e[2] = c.y & 0xFFFF; e[3] = c.y >> 16;
+            e[4] = c.z & 0xFFFF; e[5] = c.z >> 16; e[6] = c.w & 0xFFFF; e[7] = c.w >> 16;
+        }
+        int first = 8;
+#pragma unroll
+        for (int t = 7; t >= 0; --t) {
+            const int q = q0 + t;
+            if (q >= p && (q >= mlen || e[t] >= n || !is_ins(e[t]))) first = t;
+        }
+        int hit = kNone16;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (u == first) hit = e[u];
+        const unsigned bal = (__ballot_sync(gmask, first < 8) >> g0) & 0xFFu;
+        if (bal) {
+            const int src = g0 + __ffs(bal) - 1;
+            const int t = __shfl_sync(gmask, first, src);
+            const int h = __shfl_sync(gmask, hit, src);
+            if (sl == 0) {
+                const int q = base + (src - g0) * 8 + t;
+                atomicAdd(scan_chunks, 1);
+                atomicAdd(probes, 1);
+                if (q < mlen && h < n) {
+                    ptr[w] = (uint16_t)q;
+                    mc[w] = (uint16_t)h;
+                } else {
+                    ptr[w] = (uint16_t)(q < mlen ? q : mlen);
+                    mc[w] = kNone16;
+                }
+            }
+            return true;
+        }
+        if (sl == 0) {
+            atomicAdd(scan_chunks, 1);
+            atomicAdd(probes, 1);
+            ptr[w] = (uint16_t)(base + 63);  // all 64 inserted (so base + 63 < mlen)
+        }
         return false;
     }
 
@@ -457,7 +523,7 @@ struct Loop {
         for (int c0 = 0; c0 < cnt; c0 += kChunk) {
             const int m = cnt - c0 < kChunk ? cnt - c0 : kChunk;
             long long c0t = clock64();
-            if (tid == 0) { *vcount = 0; *vslow = 0; }
+            if (tid == 0) { *vcount = 0; *vslow = 0; *pcount = 0; }
             __syncthreads();
             int4 fc = make_int4(0, 0, 0, 0);
             int fe = 0;
@@ -469,16 +535,29 @@ struct Loop {
                 for (int j = 0; j < 3; ++j) {
                     const int w = vs[j];
                     const uint32_t bit = 1u << (w & 31);
-                    if (!(atomicOr(&vmark[w >> 5], bit) & bit)) vlist[atomicAdd(vcount, 1)] = w;
+                    if (!(atomicOr(&vmark[w >> 5], bit) & bit)) {
+                        vlist[atomicAdd(vcount, 1)] = w;
+                        const uint16_t mw = mc[w];
+                        if (plist && mw != kNone16 && is_ins(mw)) plist[atomicAdd(pcount, 1)] = w;
+                    }
                 }
             }
             __syncthreads();
             long long c1t = clock64();
             cyc_push += c1t - c0t;
             const int nv = *vcount;
-            for (int i = tid; i < nv; i += kLoopThreads) {
-                const int w = vlist[i];
-                if (!refresh_probe(w)) vslowlist[atomicAdd(vslow, 1)] = w;
+            if (plist) {
+                // rows whose MaxCorrs was inserted: an 8-lane group each
+                const int np = *pcount;
+                for (int i = tid >> 3; i < np; i += kLoopThreads / 8) {
+                    const int w = plist[i];
+                    if (!refresh_probe8(w) && (tid & 7) == 0) vslowlist[atomicAdd(vslow, 1)] = w;
+                }
+            } else {
+                for (int i = tid; i < nv; i += kLoopThreads) {
+                    const int w = vlist[i];
+                    if (!refresh_probe(w)) vslowlist[atomicAdd(vslow, 1)] = w;
+                }
             }
             __syncthreads();
             const int ns = *vslow;
@@ -630,7 +709,7 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Key s_root[2], s_win;
     __shared__ int s_n1[2], s_n2[2];
-    __shared__ int s_vslow;
+    __shared__ int s_vslow, s_pcount;
     __shared__ int s_nf, s_k, s_vcount, s_scan, s_evals, s_stop, s_nsel, s_fcount;
     __shared__ int s_nx, s_ninv, s_nq1, s_np, s_more;
     __shared__ int s_probes, s_wref, s_wsteps;
@@ -676,6 +755,8 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
     bind(st.ts, 1, a.leaf_stale);
     st.vlist = reinterpret_cast<int *>(smem + L.off_vlist);
     st.vslowlist = reinterpret_cast<int *>(smem + L.off_vslow);
+    st.plist = heap ? nullptr : reinterpret_cast<int *>(smem + L.off_plist);
+    st.pcount = &s_pcount;
     st.fus = reinterpret_cast<int *>(smem + L.off_fus);
     st.sel = reinterpret_cast<Key *>(smem + L.off_sel);
     st.xf = reinterpret_cast<int *>(smem + L.off_x);

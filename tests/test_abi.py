@@ -67,6 +67,9 @@ def test_argument_errors_need_no_device(lib):
     lib.dbht_cluster.argtypes = [P, P, i64, i64, ctypes.c_int32, P, P, P, P, P, i64, P, P]
     assert lib.dbht_cluster(None, None, 10, 10, 0, None, None, None, None, None, 10, None,
                             None) == 1
+    lib.tmfg_memory_latency.argtypes = [P, i64, ctypes.c_int32, ctypes.c_int32, P]
+    ns = ctypes.c_double()
+    assert lib.tmfg_memory_latency(None, 1 << 20, 10, 0, ctypes.byref(ns)) == 1
 
 
 def test_package_fails_loudly_without_a_device():

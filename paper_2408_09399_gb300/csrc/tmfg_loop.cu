@@ -124,12 +124,22 @@ struct KeyOps<double> {
 template <class KO>
 __device__ __forceinline__ typename KO::Key warp_max(typename KO::Key x)
 {
+    if constexpr (sizeof(typename KO::Key) == 8) {
+        // 64-bit key: the largest high word, then the largest low word among
+        // the lanes holding it (two warp reductions instead of five
+        // shuffle-and-compare steps)
+        const unsigned hi = (unsigned)(x >> 32), lo = (unsigned)x;
+        const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+        const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+        return ((typename KO::Key)mh << 32) | ml;
+    } else {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const typename KO::Key y = KO::shfl_xor(x, o);
-        if (KO::gt(y, x)) x = y;
+        for (int o = 16; o > 0; o >>= 1) {
+            const typename KO::Key y = KO::shfl_xor(x, o);
+            if (KO::gt(y, x)) x = y;
+        }
+        return x;
     }
-    return x;
 }
 
 // ------------------------------------------------------------- max index

@@ -576,11 +576,13 @@ struct Loop {
             __syncthreads();
             long long c2t = clock64();
             cyc_refresh += c2t - c1t;
+            // the gathers first, then the marks' clearing (needed by the next
+            // chunk or insertion only, after the barrier)
+            if (tid < m) face_best_thread(fe & 0x0FFFFFFF, fc, (fe >> 28) & 3);
             for (int i = tid; i < nv; i += kLoopThreads) {
                 const int w = vlist[i];
                 atomicAnd(&vmark[w >> 5], ~(1u << (w & 31)));
             }
-            if (tid < m) face_best_thread(fe & 0x0FFFFFFF, fc, (fe >> 28) & 3);
             __syncthreads();
             cyc_gain += clock64() - c2t;
         }

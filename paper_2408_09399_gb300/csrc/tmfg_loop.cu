@@ -272,6 +272,15 @@ struct Loop {
     // shared scalars
     int *nf, *k, *vcount, *vslow, *scan_chunks, *face_evals;
     int *probes, *warp_refreshes, *warp_steps;
+    // this thread's share of the counters, added to them once per segment
+    int n_scan = 0, n_probes = 0, n_wsteps = 0, n_evals = 0;
+    __device__ void flush_counters()
+    {
+        if (n_scan) atomicAdd(scan_chunks, n_scan);
+        if (n_probes) atomicAdd(probes, n_probes);
+        if (n_wsteps) atomicAdd(warp_steps, n_wsteps);
+        if (n_evals) atomicAdd(face_evals, n_evals);
+    }
     long long cyc_push = 0, cyc_refresh = 0, cyc_gain = 0;  // thread 0's view
 
     __device__ bool is_ins(int v) const { return (ins[v >> 5] >> (v & 31)) & 1u; }
@@ -336,8 +345,8 @@ struct Loop {
                 if (q >= p && (q >= mlen || e[t] >= n || !is_ins(e[t]))) first = t;
             }
             if (lane == 0) {
-                atomicAdd(scan_chunks, 1);
-                atomicAdd(warp_steps, 1);
+                ++n_scan;
+                ++n_wsteps;
             }
             const unsigned bal = __ballot_sync(0xffffffffu, first < 8);
             if (bal) {
@@ -391,8 +400,8 @@ struct Loop {
         for (int h = 0; h < 8; ++h)
             c[h] = base + 8 * h < a.ldi ? *reinterpret_cast<const uint4 *>(row + base + 8 * h)
                                         : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-        atomicAdd(scan_chunks, 1);
-        atomicAdd(probes, 1);
+        ++n_scan;
+        ++n_probes;
         // all 64 checks independent (their shared-memory reads overlap); the
         // first candidate wins
         int first = 64, hit = kNone16;
@@ -463,8 +472,8 @@ struct Loop {
             const int h = __shfl_sync(gmask, hit, src);
             if (sl == 0) {
                 const int q = base + (src - g0) * 8 + t;
-                atomicAdd(scan_chunks, 1);
-                atomicAdd(probes, 1);
+                ++n_scan;
+                ++n_probes;
                 if (q < mlen && h < n) {
                     ptr[w] = (uint16_t)q;
                     mc[w] = (uint16_t)h;
@@ -476,8 +485,8 @@ struct Loop {
             return true;
         }
         if (sl == 0) {
-            atomicAdd(scan_chunks, 1);
-            atomicAdd(probes, 1);
+            ++n_scan;
+            ++n_probes;
             ptr[w] = (uint16_t)(base + 63);  // all 64 inserted (so base + 63 < mlen)
         }
         return false;
@@ -520,7 +529,7 @@ struct Loop {
                 tf.set(f, KO::empty());
             }
         }
-        atomicAdd(face_evals, 1);
+        ++n_evals;
     }
 
     // Recompute the faces of the face-update list [0..cnt): entry = face |
@@ -1242,6 +1251,7 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
         }
     }
     // ---- statistics (summed over segments) and the state for the next segment
+    st.flush_counters();
     __syncthreads();
     if (tid == 0) {
         if (s_stop) set_status(a.status, s_stop);

@@ -546,19 +546,44 @@ struct Loop {
             __syncthreads();
             int4 fc = make_int4(0, 0, 0, 0);
             int fe = 0;
+            // thread t keeps face t for its evaluation; the marks of the
+            // 3m (face, vertex) pairs are spread over all threads, one
+            // dependent chain of shared-memory atomics each
+            const int np3 = 3 * m;
+            int pf[2], pj[2];
+            int4 pc[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int q = tid + r * kLoopThreads;
+                pf[r] = q < np3 ? fu_get(c0 + q / 3) & 0x0FFFFFFF : -1;
+                pj[r] = q % 3;
+            }
             if (tid < m) {
                 fe = fu_get(c0 + tid);
                 fc = a.face[fe & 0x0FFFFFFF];
-                const int vs[3] = {fc.x, fc.y, fc.z};
+            }
 #pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const int w = vs[j];
-                    const uint32_t bit = 1u << (w & 31);
-                    if (!(atomicOr(&vmark[w >> 5], bit) & bit)) {
-                        vlist[atomicAdd(vcount, 1)] = w;
-                        const uint16_t mw = mc[w];
-                        if (plist && mw != kNone16 && is_ins(mw)) plist[atomicAdd(pcount, 1)] = w;
-                    }
+            for (int r = 0; r < 2; ++r) pc[r] = pf[r] >= 0 ? a.face[pf[r]] : make_int4(0, 0, 0, 0);
+            for (int q = tid + 2 * kLoopThreads; q < np3; q += kLoopThreads) {
+                // more than 2 pairs per thread: only for chunks of over 170 faces
+                const int4 c = a.face[fu_get(c0 + q / 3) & 0x0FFFFFFF];
+                const int w = q % 3 == 0 ? c.x : q % 3 == 1 ? c.y : c.z;
+                const uint32_t bit = 1u << (w & 31);
+                if (!(atomicOr(&vmark[w >> 5], bit) & bit)) {
+                    vlist[atomicAdd(vcount, 1)] = w;
+                    const uint16_t mw = mc[w];
+                    if (plist && mw != kNone16 && is_ins(mw)) plist[atomicAdd(pcount, 1)] = w;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                if (pf[r] < 0) continue;
+                const int w = pj[r] == 0 ? pc[r].x : pj[r] == 1 ? pc[r].y : pc[r].z;
+                const uint32_t bit = 1u << (w & 31);
+                if (!(atomicOr(&vmark[w >> 5], bit) & bit)) {
+                    vlist[atomicAdd(vcount, 1)] = w;
+                    const uint16_t mw = mc[w];
+                    if (plist && mw != kNone16 && is_ins(mw)) plist[atomicAdd(pcount, 1)] = w;
                 }
             }
             __syncthreads();

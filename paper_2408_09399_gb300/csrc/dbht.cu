@@ -726,6 +726,8 @@ __device__ void linkage_cta(int m, float *dm, int *id_g, int *rep_g, int *sz_g,
 // sequential order does.  Each chain step is one row scan by the whole CTA
 // (no row minima to keep current), a merge one more pass over rows a and b.
 constexpr int kChainMax = 2048;
+// keys (8 B) and six int arrays per item, inside the linkage kernels' shared memory
+static_assert(32 * (size_t)kChainMax <= kLkSmem, "chain state exceeds the linkage shared memory");
 constexpr int kChainUnroll = 8;   // row entries per thread in flight (m <= 2048)
 __device__ void linkage_chain_cta(int m, float *dm, const int *id_g, const int *rep_g,
                                   const int *sz_g, int n, int row0, double *Z, int *status,

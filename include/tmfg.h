@@ -356,9 +356,13 @@ int tmfg_serve_plan(const int64_t *n, int32_t count, int32_t apsp, int32_t max_b
  *   status: caller-owned device int32; the call sets it to 0 and the
  *           kernels record the first data error in it (read it after the
  *           stream reaches this call).
- * Runs on the current CUDA device.  The first call on a device looks up the
- * scratch array's device address; make that first call before any stream
- * capture.  All calls share the one array and it keeps the last call's
+ * Runs on the current CUDA device, in the context current on the calling
+ * thread: every call looks up the scratch array's device address in that
+ * context (so a device reset or another current context is handled); the
+ * first call on a device also reads its SM count.  Make the first call on
+ * a device before any stream capture.  Device loops stop after the time
+ * limit that tmfg_create uses (60 s, or TMFG_TIMEOUT_MS milliseconds from
+ * the environment).  All calls share the one array and it keeps the last call's
  * contents (the call clears what must start at zero): calls whose kernels
  * overlap on the GPU, on different streams or threads, race and corrupt
  * each other's results -- order them on one stream.

@@ -36,11 +36,61 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    compile_library(_SRC, tmp)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+def compile_library(src: str, out: str) -> str:
+    """gcc flags of the oracle: OpenMP on, no FMA contraction, no fast-math."""
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared", "-o", out, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    return out
+
+
+def _bind(lib):
+    """Declare the argument and result types of every entry point."""
+    P = ctypes.c_void_p
+    i64 = ctypes.c_int64
+    ci = ctypes.c_int
+    lib.oracle_set_threads.argtypes = [ci]
+    lib.oracle_set_threads.restype = ci
+    lib.oracle_quantize.argtypes = [ctypes.c_double]
+    lib.oracle_quantize.restype = i64
+    lib.oracle_rowsums.argtypes = [P, i64, i64, ci, P]
+    lib.oracle_rowsums.restype = None
+    lib.oracle_rowsort.argtypes = [P, i64, i64, ci, P]
+    lib.oracle_rowsort.restype = ci
+    lib.oracle_tmfg.argtypes = [P, i64, i64, ci, ci, i64, ci, P, P, P, P, P, P, P, P]
+    lib.oracle_tmfg.restype = ci
+    lib.oracle_apsp_exact.argtypes = [P, i64, i64, ci, P, i64, ci, P]
+    lib.oracle_apsp_exact.restype = ci
+    lib.oracle_sssp_rows.argtypes = [P, i64, i64, ci, P, i64, ci, P, i64, P]
+    lib.oracle_sssp_rows.restype = ci
+    lib.oracle_sssp_bounded_rows.argtypes = [P, i64, i64, ci, P, i64, ci, P, P, i64, P]
+    lib.oracle_sssp_bounded_rows.restype = ci
+    lib.oracle_rowsort_rows.argtypes = [P, i64, i64, ci, P, i64, P]
+    lib.oracle_rowsort_rows.restype = ci
+    lib.oracle_hubs.argtypes = [i64, P, i64, i64, P]
+    lib.oracle_hubs.restype = ci
+    lib.oracle_apsp_approx.argtypes = [P, i64, i64, ci, P, i64, i64, ctypes.c_double, ci,
+                                       P, P, P, P]
+    lib.oracle_apsp_approx.restype = ci
+    lib.oracle_apsp_approx_rows.argtypes = [P, i64, i64, ci, P, i64, i64, ctypes.c_double, ci,
+                                            P, i64, P]
+    lib.oracle_apsp_approx_rows.restype = ci
+    lib.oracle_complete_linkage.argtypes = [P, i64, P]
+    lib.oracle_complete_linkage.restype = ci
+    lib.oracle_dbht.argtypes = [P, i64, i64, ci, P, P, P, P, P, P, P, P, P, P]
+    lib.oracle_dbht.restype = ci
+    lib.oracle_cut.argtypes = [P, i64, i64, P]
+    lib.oracle_cut.restype = ci
+    lib.oracle_ari.argtypes = [P, P, i64]
+    lib.oracle_ari.restype = ctypes.c_double
+    lib.oracle_pearson.argtypes = [P, i64, i64, ci, P]
+    lib.oracle_pearson.restype = ci
+    return lib
 
 
 def _load():
@@ -48,43 +98,29 @@ def _load():
     with _lock:
         if _lib is None:
             build()
-            lib = ctypes.CDLL(_LIB_PATH)
-            P = ctypes.c_void_p
-            i64 = ctypes.c_int64
-            ci = ctypes.c_int
-            lib.oracle_quantize.argtypes = [ctypes.c_double]
-            lib.oracle_quantize.restype = i64
-            lib.oracle_rowsums.argtypes = [P, i64, i64, ci, P]
-            lib.oracle_rowsums.restype = None
-            lib.oracle_rowsort.argtypes = [P, i64, i64, ci, P]
-            lib.oracle_rowsort.restype = ci
-            lib.oracle_tmfg.argtypes = [P, i64, i64, ci, ci, i64, ci, P, P, P, P, P, P, P, P]
-            lib.oracle_tmfg.restype = ci
-            lib.oracle_apsp_exact.argtypes = [P, i64, i64, ci, P, i64, ci, P]
-            lib.oracle_apsp_exact.restype = ci
-            lib.oracle_sssp_rows.argtypes = [P, i64, i64, ci, P, i64, ci, P, i64, P]
-            lib.oracle_sssp_rows.restype = ci
-            lib.oracle_sssp_bounded_rows.argtypes = [P, i64, i64, ci, P, i64, ci, P, P, i64, P]
-            lib.oracle_sssp_bounded_rows.restype = ci
-            lib.oracle_rowsort_rows.argtypes = [P, i64, i64, ci, P, i64, P]
-            lib.oracle_rowsort_rows.restype = ci
-            lib.oracle_hubs.argtypes = [i64, P, i64, i64, P]
-            lib.oracle_hubs.restype = ci
-            lib.oracle_apsp_approx.argtypes = [P, i64, i64, ci, P, i64, i64, ctypes.c_double, ci,
-                                               P, P, P, P]
-            lib.oracle_apsp_approx.restype = ci
-            lib.oracle_complete_linkage.argtypes = [P, i64, P]
-            lib.oracle_complete_linkage.restype = ci
-            lib.oracle_dbht.argtypes = [P, i64, i64, ci, P, P, P, P, P, P, P, P, P, P]
-            lib.oracle_dbht.restype = ci
-            lib.oracle_cut.argtypes = [P, i64, i64, P]
-            lib.oracle_cut.restype = ci
-            lib.oracle_ari.argtypes = [P, P, i64]
-            lib.oracle_ari.restype = ctypes.c_double
-            lib.oracle_pearson.argtypes = [P, i64, i64, ci, P]
-            lib.oracle_pearson.restype = ci
-            _lib = lib
+            _lib = _bind(ctypes.CDLL(_LIB_PATH))
     return _lib
+
+
+class use_library:
+    """Context manager for the oracle's own tests: route every call of this
+    module through another build of the oracle (a library compiled from a
+    copy of ``tmfg_oracle.c`` with one planted mistake), then restore."""
+
+    def __init__(self, path: str):
+        self.lib = _bind(ctypes.CDLL(path))
+
+    def __enter__(self):
+        global _lib
+        _load()
+        with _lock:
+            self.saved, _lib = _lib, self.lib
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        with _lock:
+            _lib = self.saved
 
 
 def _ptr(a):
@@ -103,6 +139,12 @@ def _mat(S):
     if S.dtype == np.float64:
         return S, F64
     raise TypeError("S must be float32 or float64")
+
+
+def set_threads(k: int = 0) -> int:
+    """Host threads for the oracle's parallel loops (k < 1: unchanged);
+    returns the number in use."""
+    return int(_load().oracle_set_threads(int(k)))
 
 
 def quantize(x: float) -> int:
@@ -131,7 +173,8 @@ def tmfg(S, mode: str = "heap", prefix: int = 1, maxcorrs_bruteforce: bool = Fal
     """TMFG by corr-tmfg (Algorithm 1), heap-tmfg (Algorithm 2) or the exact
     greedy ('exact').  Returns a dict of numpy arrays: order (n), edges
     (3n-6, 2), ins_face (n-4, 3), parent (n-3), ins_gain (n-4), rowsum (n),
-    faces (2n-4, 3) and stats {face_evals, stale_pops}."""
+    faces (2n-4, 3) and stats {face_evals, stale_pops, and the wall time in ns of
+    the row sums + clique, the row sort and the insertion loop}."""
     S, dt = _mat(S)
     n = S.shape[0]
     m = {"corr": CORR, "heap": HEAP, "exact": EXACT_GREEDY}[mode]
@@ -142,7 +185,7 @@ def tmfg(S, mode: str = "heap", prefix: int = 1, maxcorrs_bruteforce: bool = Fal
     ins_gain = np.empty(n - 4, np.float64)
     rs = np.empty(n, np.int64)
     faces = np.empty((2 * n - 4, 3), np.int32)
-    stats = np.zeros(2, np.int64)
+    stats = np.zeros(5, np.int64)
     rc = _load().oracle_tmfg(_ptr(S), n, S.shape[1], dt, m, int(prefix),
                              1 if maxcorrs_bruteforce else 0, _ptr(order), _ptr(edges),
                              _ptr(ins_face), _ptr(parent), _ptr(ins_gain), _ptr(rs),
@@ -150,7 +193,9 @@ def tmfg(S, mode: str = "heap", prefix: int = 1, maxcorrs_bruteforce: bool = Fal
     _check(rc, "tmfg")
     return {"order": order, "edges": edges, "ins_face": ins_face, "parent": parent,
             "ins_gain": ins_gain, "rowsum": rs, "faces": faces,
-            "stats": {"face_evals": int(stats[0]), "stale_pops": int(stats[1])}}
+            "stats": {"face_evals": int(stats[0]), "stale_pops": int(stats[1]),
+                      "ns_rowsums_clique": int(stats[2]), "ns_rowsort": int(stats[3]),
+                      "ns_loop": int(stats[4])}}
 
 
 def apsp_exact(S, edges, prec: int = 64):
@@ -225,6 +270,21 @@ def apsp_approx(S, edges, n_hubs: int = 0, radius_factor: float = 2.0, prec: int
                                       h, float(radius_factor), prec, _ptr(D), _ptr(hb),
                                       _ptr(near), _ptr(dnear)), "apsp_approx")
     return D, {"hubs": hb, "nearest": near, "dnear": dnear}
+
+
+def apsp_approx_rows(S, edges, sources, n_hubs: int = 0, radius_factor: float = 2.0,
+                     prec: int = 32):
+    """Rows ``sources`` of apsp_approx (same arguments) without its n x n
+    work matrix: (len(sources), n) float64."""
+    S, dt = _mat(S)
+    n = S.shape[0]
+    e = np.ascontiguousarray(edges, np.int32)
+    src = np.ascontiguousarray(sources, np.int32)
+    D = np.empty((len(src), n), np.float64)
+    _check(_load().oracle_apsp_approx_rows(_ptr(S), n, S.shape[1], dt, _ptr(e), e.shape[0],
+                                           int(n_hubs), float(radius_factor), prec, _ptr(src),
+                                           len(src), _ptr(D)), "apsp_approx_rows")
+    return D
 
 
 def complete_linkage(D):

@@ -58,6 +58,10 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_F32 0
 #define OR_F64 1
@@ -70,6 +74,27 @@
 #define OR_OK 0
 #define OR_EINVAL 1
 #define OR_ENOMEM 2
+
+/* Host threads used by the parallel loops (rows of the sort, sources of
+ * the APSP); k < 1 leaves the setting alone.  Returns the number in use. */
+int oracle_set_threads(int k)
+{
+#ifdef _OPENMP
+    if (k > 0) omp_set_num_threads(k);
+    return omp_get_max_threads();
+#else
+    (void)k;
+    return 1;
+#endif
+}
+
+/* Monotonic clock in nanoseconds (phase timings of oracle_tmfg). */
+static int64_t now_ns(void)
+{
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (int64_t)ts.tv_sec * 1000000000 + ts.tv_nsec;
+}
 
 /* ------------------------------------------------------------------ */
 /* matrix access                                                        */
@@ -556,8 +581,10 @@ int oracle_tmfg(const void *S, int64_t n, int64_t ld, int dtype, int mode, int64
     if (mode == OR_HEAP && P != 1) return OR_EINVAL;
     if (mode != OR_CORR && mode != OR_HEAP && mode != 2) return OR_EINVAL;
     tstate st;
+    const int64_t t0 = now_ns();
     int rc = tstate_init(&st, S, n, ld, dtype, order, edges, ins_face, parent, ins_gain, rowsum);
     if (rc) return rc;
+    const int64_t t1 = now_ns();
     int32_t *idx = NULL;
     if (mode != 2 && !(flags & 1)) {
         idx = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * (size_t)(n - 1));
@@ -565,16 +592,23 @@ int oracle_tmfg(const void *S, int64_t n, int64_t ld, int dtype, int mode, int64
         rc = oracle_rowsort(S, n, ld, dtype, idx);
         if (rc) { free(idx); tstate_free(&st); return rc; }
     }
+    const int64_t t2 = now_ns();
     st.idx = idx;
     st.mc_bruteforce = (flags & 1);
     if (mode == OR_CORR) rc = run_corr(&st, P);
     else if (mode == OR_HEAP) rc = run_heap(&st);
     else run_exact_greedy(&st);
+    const int64_t t3 = now_ns();
     if (faces)
         for (int64_t f = 0; f < st.nf; ++f) {
             faces[3 * f] = st.fa[f]; faces[3 * f + 1] = st.fb[f]; faces[3 * f + 2] = st.fc[f];
         }
-    if (stats) { stats[0] = st.face_evals; stats[1] = st.stale_pops; }
+    /* stats: face evaluations, stale pops, then the wall time (ns) of the
+       row sums + initial clique, the row sort and the insertion loop */
+    if (stats) {
+        stats[0] = st.face_evals; stats[1] = st.stale_pops;
+        stats[2] = t1 - t0; stats[3] = t2 - t1; stats[4] = t3 - t2;
+    }
     free(idx);
     tstate_free(&st);
     return rc;
@@ -743,12 +777,19 @@ int oracle_sssp_rows(const void *S, int64_t n, int64_t ld, int dtype, const int3
     graph_t g;
     int rc = build_graph(&m, n, edges, ne, prec, &g);
     if (rc) return rc;
-    uint8_t *done = (uint8_t *)malloc((size_t)n);
-    dent_t *heap = (dent_t *)malloc(sizeof(dent_t) * (size_t)(2 * ne + n + 1));
-    if (!done || !heap) rc = OR_ENOMEM;
-    for (int64_t i = 0; i < nsrc && !rc; ++i)
-        dijkstra(&g, src[i], prec, -1.0, D + i * n, done, heap);
-    free(done); free(heap);
+#pragma omp parallel
+    {
+        uint8_t *done = (uint8_t *)malloc((size_t)n);
+        dent_t *heap = (dent_t *)malloc(sizeof(dent_t) * (size_t)(2 * ne + n + 1));
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t i = 0; i < nsrc; ++i)
+            if (done && heap) dijkstra(&g, src[i], prec, -1.0, D + i * n, done, heap);
+        if (!done || !heap) {
+#pragma omp atomic write
+            rc = OR_ENOMEM;
+        }
+        free(done); free(heap);
+    }
     graph_free(&g);
     return rc;
 }
@@ -765,12 +806,19 @@ int oracle_sssp_bounded_rows(const void *S, int64_t n, int64_t ld, int dtype,
     graph_t g;
     int rc = build_graph(&m, n, edges, ne, prec, &g);
     if (rc) return rc;
-    uint8_t *done = (uint8_t *)malloc((size_t)n);
-    dent_t *heap = (dent_t *)malloc(sizeof(dent_t) * (size_t)(2 * ne + n + 1));
-    if (!done || !heap) rc = OR_ENOMEM;
-    for (int64_t i = 0; i < nsrc && !rc; ++i)
-        dijkstra(&g, src[i], prec, bound[i], D + i * n, done, heap);
-    free(done); free(heap);
+#pragma omp parallel
+    {
+        uint8_t *done = (uint8_t *)malloc((size_t)n);
+        dent_t *heap = (dent_t *)malloc(sizeof(dent_t) * (size_t)(2 * ne + n + 1));
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t i = 0; i < nsrc; ++i)
+            if (done && heap) dijkstra(&g, src[i], prec, bound[i], D + i * n, done, heap);
+        if (!done || !heap) {
+#pragma omp atomic write
+            rc = OR_ENOMEM;
+        }
+        free(done); free(heap);
+    }
     graph_free(&g);
     return rc;
 }
@@ -834,14 +882,26 @@ int oracle_apsp_approx(const void *S, int64_t n, int64_t ld, int dtype, const in
     int32_t *hn = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     double *dn = (double *)malloc(sizeof(double) * (size_t)n);
     double *rad = (double *)malloc(sizeof(double) * (size_t)n);
-    uint8_t *done = (uint8_t *)malloc((size_t)n);
-    dent_t *heap = (dent_t *)malloc(sizeof(dent_t) * (size_t)(2 * ne + n + 1));
     double *B = (double *)malloc(sizeof(double) * (size_t)(n * n));
-    if (!hubs || !DH || !hn || !dn || !rad || !done || !heap || !B) { rc = OR_ENOMEM; goto out; }
+    if (!hubs || !DH || !hn || !dn || !rad || !B) { rc = OR_ENOMEM; goto out; }
     rc = oracle_hubs(n, edges, ne, h, hubs);
     if (rc) goto out;
-    /* exact SSSP from every hub */
-    for (int64_t i = 0; i < h; ++i) dijkstra(&g, hubs[i], prec, -1.0, DH + i * n, done, heap);
+    /* exact SSSP from every hub, then (below) the bounded searches: each
+       search is independent, so they run on all host threads */
+#pragma omp parallel
+    {
+        uint8_t *done = (uint8_t *)malloc((size_t)n);
+        dent_t *heap = (dent_t *)malloc(sizeof(dent_t) * (size_t)(2 * ne + n + 1));
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t i = 0; i < h; ++i)
+            if (done && heap) dijkstra(&g, hubs[i], prec, -1.0, DH + i * n, done, heap);
+        if (!done || !heap) {
+#pragma omp atomic write
+            rc = OR_ENOMEM;
+        }
+        free(done); free(heap);
+    }
+    if (rc) goto out;
     /* nearest hub and radius of every source */
     for (int64_t s = 0; s < n; ++s) {
         int32_t bi = 0;
@@ -852,7 +912,21 @@ int oracle_apsp_approx(const void *S, int64_t n, int64_t ld, int dtype, const in
         rad[s] = prec == 32 ? (double)((float)rf * (float)dn[s]) : rf * dn[s];
     }
     /* bounded exact search from every source */
-    for (int64_t s = 0; s < n; ++s) dijkstra(&g, (int32_t)s, prec, rad[s], B + s * n, done, heap);
+#pragma omp parallel
+    {
+        uint8_t *done = (uint8_t *)malloc((size_t)n);
+        dent_t *heap = (dent_t *)malloc(sizeof(dent_t) * (size_t)(2 * ne + n + 1));
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t s = 0; s < n; ++s)
+            if (done && heap) dijkstra(&g, (int32_t)s, prec, rad[s], B + s * n, done, heap);
+        if (!done || !heap) {
+#pragma omp atomic write
+            rc = OR_ENOMEM;
+        }
+        free(done); free(heap);
+    }
+    if (rc) goto out;
+#pragma omp parallel for schedule(static)
     for (int64_t s = 0; s < n; ++s)
         for (int64_t t = 0; t < n; ++t) {
             double est_s, est_t, v;
@@ -872,7 +946,97 @@ int oracle_apsp_approx(const void *S, int64_t n, int64_t ld, int dtype, const in
     if (nearest_out) memcpy(nearest_out, hn, sizeof(int32_t) * (size_t)n);
     if (dnear_out) memcpy(dnear_out, dn, sizeof(double) * (size_t)n);
 out:
-    free(hubs); free(DH); free(hn); free(dn); free(rad); free(done); free(heap); free(B);
+    free(hubs); free(DH); free(hn); free(dn); free(rad); free(B);
+    graph_free(&g);
+    return rc;
+}
+
+/* Rows of the approximate APSP (Section 4.3; reading R12) for the listed
+ * sources only: row i of D (nsrc x n) equals row src[i] of oracle_apsp_approx
+ * with the same arguments, without its n x n work matrix.  The bounded search
+ * from every vertex t still runs (its distance to a listed source enters
+ * D[s,t] when within t's radius); only those distances are kept. */
+int oracle_apsp_approx_rows(const void *S, int64_t n, int64_t ld, int dtype,
+                            const int32_t *edges, int64_t ne, int64_t n_hubs, double rf,
+                            int prec, const int32_t *src, int64_t nsrc, double *D)
+{
+    if (n < 1 || nsrc < 0 || (prec != 32 && prec != 64)) return OR_EINVAL;
+    for (int64_t i = 0; i < nsrc; ++i)
+        if (src[i] < 0 || src[i] >= n) return OR_EINVAL;
+    int64_t h = n_hubs > 0 ? n_hubs : (int64_t)ceil(sqrt((double)n));
+    if (h > n) h = n;
+    if (!(rf > 0.0)) rf = 2.0;
+    mat_t m = {S, n, ld, dtype};
+    graph_t g;
+    int rc = build_graph(&m, n, edges, ne, prec, &g);
+    if (rc) return rc;
+    int32_t *hubs = (int32_t *)malloc(sizeof(int32_t) * (size_t)h);
+    double *DH = (double *)malloc(sizeof(double) * (size_t)(h * n));
+    int32_t *hn = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    double *dn = (double *)malloc(sizeof(double) * (size_t)n);
+    double *rad = (double *)malloc(sizeof(double) * (size_t)n);
+    double *Bs = (double *)malloc(sizeof(double) * (size_t)(nsrc * n + 1)); /* from s */
+    double *Bt = (double *)malloc(sizeof(double) * (size_t)(nsrc * n + 1)); /* from t, at s */
+    if (!hubs || !DH || !hn || !dn || !rad || !Bs || !Bt) { rc = OR_ENOMEM; goto out; }
+    rc = oracle_hubs(n, edges, ne, h, hubs);
+    if (rc) goto out;
+#pragma omp parallel
+    {
+        uint8_t *done = (uint8_t *)malloc((size_t)n);
+        dent_t *heap = (dent_t *)malloc(sizeof(dent_t) * (size_t)(2 * ne + n + 1));
+        double *row = (double *)malloc(sizeof(double) * (size_t)n);
+        int ok = done && heap && row;
+        /* exact SSSP from every hub */
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t i = 0; i < h; ++i)
+            if (ok) dijkstra(&g, hubs[i], prec, -1.0, DH + i * n, done, heap);
+        /* nearest hub and radius of every vertex */
+#pragma omp for schedule(static)
+        for (int64_t s = 0; s < n; ++s) {
+            int32_t bi = 0;
+            for (int64_t i = 1; i < h; ++i)
+                if (DH[i * n + s] < DH[bi * n + s]) bi = (int32_t)i;
+            hn[s] = bi;
+            dn[s] = DH[bi * n + s];
+            rad[s] = prec == 32 ? (double)((float)rf * (float)dn[s]) : rf * dn[s];
+        }
+        /* bounded searches from the listed sources, and from every vertex t
+           with only its distances to the listed sources kept */
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t i = 0; i < nsrc; ++i)
+            if (ok) dijkstra(&g, src[i], prec, rad[src[i]], Bs + i * n, done, heap);
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t t = 0; t < n; ++t) {
+            if (!ok) continue;
+            dijkstra(&g, (int32_t)t, prec, rad[t], row, done, heap);
+            for (int64_t i = 0; i < nsrc; ++i) Bt[i * n + t] = row[src[i]];
+        }
+        if (!ok) {
+#pragma omp atomic write
+            rc = OR_ENOMEM;
+        }
+        free(done); free(heap); free(row);
+    }
+    if (rc) goto out;
+    for (int64_t i = 0; i < nsrc; ++i) {
+        const int64_t s = src[i];
+        for (int64_t t = 0; t < n; ++t) {
+            double est_s, est_t, v;
+            if (prec == 32) {
+                est_s = (double)((float)dn[s] + (float)DH[(int64_t)hn[s] * n + t]);
+                est_t = (double)((float)dn[t] + (float)DH[(int64_t)hn[t] * n + s]);
+            } else {
+                est_s = dn[s] + DH[(int64_t)hn[s] * n + t];
+                est_t = dn[t] + DH[(int64_t)hn[t] * n + s];
+            }
+            v = est_s < est_t ? est_s : est_t;
+            if (Bs[i * n + t] <= rad[s] && Bs[i * n + t] < v) v = Bs[i * n + t];
+            if (Bt[i * n + t] <= rad[t] && Bt[i * n + t] < v) v = Bt[i * n + t];
+            D[i * n + t] = v;
+        }
+    }
+out:
+    free(hubs); free(DH); free(hn); free(dn); free(rad); free(Bs); free(Bt);
     graph_free(&g);
     return rc;
 }

@@ -44,6 +44,16 @@ using namespace tmfg;
 
 namespace tmfg {
 
+unsigned long long device_timeout_ns()
+{
+    unsigned long long ns = 60ull * 1000000000ull;
+    if (const char *e = std::getenv("TMFG_TIMEOUT_MS")) {
+        const long long ms = std::atoll(e);
+        if (ms > 0) ns = (unsigned long long)ms * 1000000ull;
+    }
+    return ns;
+}
+
 int ensure_work(tmfg_ctx *c, size_t bytes, cudaStream_t stream)
 {
     if (bytes <= c->work_bytes) return TMFG_OK;
@@ -260,11 +270,7 @@ int tmfg_create(tmfg_ctx **out, int device, size_t workspace_budget_bytes)
         delete c;
         return TMFG_ECUDA;
     }
-    c->timeout_ns = 60ull * 1000000000ull;
-    if (const char *e = std::getenv("TMFG_TIMEOUT_MS")) {
-        const long long ms = std::atoll(e);
-        if (ms > 0) c->timeout_ns = (unsigned long long)ms * 1000000ull;
-    }
+    c->timeout_ns = device_timeout_ns();
     *out = c;
     return TMFG_OK;
 }

@@ -766,11 +766,13 @@ static __device__ __align__(256) unsigned char g_apsp_scratch[kNoAllocBytes];
 namespace {
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[kNoAllocMaxDevices];
 int g_noalloc_sms[kNoAllocMaxDevices];
 
-// Device address of the scratch array and the SM count of the current
-// device, looked up on the first call for that device.
+// Device address of the scratch array in the context current on the calling
+// thread, and the SM count of the current device.  The address is looked up
+// on every call (a host-side table lookup once the module is loaded), so it
+// stays right after a device reset or with a different context current; only
+// the SM count, a property of the device, is kept between calls.
 int noalloc_setup(void **ptr, int *sms)
 {
     int dev = -1;
@@ -778,19 +780,22 @@ int noalloc_setup(void **ptr, int *sms)
         cudaGetLastError();
         return TMFG_ECUDA;
     }
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_apsp_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return TMFG_ECUDA;
+    }
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
+    if (!g_noalloc_sms[dev]) {
         int s = 0;
-        if (cudaGetSymbolAddress(&p, g_apsp_scratch) != cudaSuccess || !p ||
-            cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        if (cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            s <= 0) {
             cudaGetLastError();
             return TMFG_ECUDA;
         }
-        g_noalloc_ptr[dev] = p;
         g_noalloc_sms[dev] = s;
     }
-    *ptr = g_noalloc_ptr[dev];
+    *ptr = p;
     *sms = g_noalloc_sms[dev];
     return TMFG_OK;
 }
@@ -806,6 +811,8 @@ extern "C" int tmfg_apsp_exact_noalloc(const void *S, int64_t n, int64_t ld, int
     if (!S || !edges || !D || !status || n < 4 || ld < n || ldd < n) return TMFG_EINVAL;
     if (dtype != TMFG_F32 && dtype != TMFG_F64) return TMFG_EINVAL;
     if (n > TMFG_NOALLOC_MAX_N || sssp_smem_bytes((int)n) > kSmemLimit) return TMFG_ETOOBIG;
+    // the exact path's carve of the workspace must fit the static array
+    if (apsp_work_bytes((int)n, 0, 1) > kNoAllocBytes) return TMFG_EINTERNAL;
     void *work = nullptr;
     int sms = 0;
     int rc = noalloc_setup(&work, &sms);
@@ -815,5 +822,5 @@ extern "C" int tmfg_apsp_exact_noalloc(const void *S, int64_t n, int64_t ld, int
     // launch_apsp itself before they are accumulated
     if (cudaMemsetAsync(status, 0, sizeof(int32_t), st) != cudaSuccess) return TMFG_ECUDA;
     return launch_apsp(S, (int)n, ld, dtype, edges, 0, 0, 0.0f, D, ldd, work, status, sms,
-                       60ull * 1000000000ull, st);
+                       device_timeout_ns(), st);
 }

@@ -5,6 +5,10 @@
 
 namespace tmfg {
 
+// api.cu: the time limit of every device loop, 60 s unless the environment
+// variable TMFG_TIMEOUT_MS gives a positive number of milliseconds
+unsigned long long device_timeout_ns();
+
 // rowsort.cu
 struct SortJob {  // the rows of one matrix, for the batched sort
     const void *S;

@@ -241,3 +241,33 @@ def test_dbht_full_size_n20000(T, ctx):
     for g in np.unique(group):
         assert len(np.unique(roots[group == g])) == 1
     assert len(np.unique(roots)) == ng
+
+
+def test_dbht_hand_traced_case(T, ctx):
+    """The hand-traced DBHT case (given TMFG, S on its edges, integer D):
+    directions, converging bubbles, groups, bubbles and linkage on the
+    device equal the values worked out by hand, as they do in the oracle."""
+    import json
+    import os
+    case = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "hand_traced_dbht.json")))
+    n = case["n"]
+    S = np.eye(n, dtype=np.float32)
+    for key, val in case["S_edges_64ths"].items():
+        i, j = map(int, key.split(","))
+        S[i, j] = S[j, i] = val / 64.0
+    D = np.zeros((n, n), np.float32)
+    for key, val in case["D_upper"].items():
+        i, j = map(int, key.split(","))
+        D[i, j] = D[j, i] = val
+    tg = {"order": case["tmfg"]["order"], "edges": case["tmfg"]["edges"],
+          "ins_face": case["tmfg"]["ins_face"], "bubble_parent": case["tmfg"]["parent"]}
+    td = {k: torch.tensor(v, dtype=torch.int32, device="cuda:0") for k, v in tg.items()}
+    Z, info = T.dbht_cluster_detail(ctx, dev(S), td, dev(D))
+    assert T.tmfg_sync_status(ctx) == 0
+    e = case["expect"]
+    assert info["direction"].cpu().tolist() == e["direction"]
+    assert info["converging"].cpu().tolist() == e["converging"]
+    assert info["group"].cpu().tolist() == e["group"]
+    assert info["bubble"].cpu().tolist() == e["bubble"]
+    assert Z.cpu().tolist() == [[float(x) for x in row] for row in e["linkage"]]

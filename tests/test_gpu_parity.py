@@ -236,32 +236,55 @@ def test_argument_errors(T, ctx):
 
 # ------------------------------------------------------------------ full size
 
-@pytest.mark.slow
-def test_full_size_n20000(T, ctx):
-    """The n=20000 workload in the benchmark's launch configuration: the
-    whole heap TMFG is compared with the oracle; APSP rows of 48 sampled
-    sources are compared bit for bit; the approximate matrix is checked for
-    its defining properties on sampled rows."""
+@pytest.fixture(scope="module")
+def full_size(T):
+    """The n=20000 workload of the benchmark (50 planted clusters, Student-t(4)
+    noise, float32 Pearson S), on the device and on the host."""
     S, _ = W.config_similarity(3, device="cuda")
-    Sn = S.cpu().numpy()
-    out = T.tmfg_build(ctx, S, "heap")
-    D = T.tmfg_apsp(ctx, S, out["edges"])
+    return S, S.cpu().numpy()
+
+
+FULL_SRC = np.unique(np.concatenate([[0, 19999], np.random.default_rng(0).integers(0, 20000, 46)]))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mode,P", [("corr", 1), ("corr", 10), ("heap", 1)])
+def test_full_size_n20000_tmfg(T, ctx, full_size, mode, P):
+    """The n=20000 workload in the benchmark's launch configuration: the
+    whole TMFG of every build mode the benchmark times (corr-tmfg prefix 1
+    is the timed step; prefix 10 and heap-tmfg are reported beside it) equals
+    the oracle's, order, edges, faces used and bubble parents."""
+    S, Sn = full_size
+    out = T.tmfg_build(ctx, S, mode, P)
     T.tmfg_sync_status(ctx)
-    ref = oracle.tmfg(Sn, "heap")
+    ref = oracle.tmfg(Sn, mode, P)
     got = {k: v.cpu().numpy() for k, v in out.items()}
-    assert_tmfg_equal(got, ref, "n=20000 heap")
-    rng = np.random.default_rng(0)
-    src = np.unique(np.concatenate([[0, 19999], rng.integers(0, 20000, 46)]))
-    Dr = oracle.sssp_rows(Sn, ref["edges"], src, prec=32)
-    assert np.array_equal(D[torch.as_tensor(src, device="cuda:0")].cpu().numpy().astype(np.float64), Dr)
+    assert_tmfg_equal(got, ref, f"n=20000 {mode} P={P}")
+
+
+@pytest.mark.slow
+def test_full_size_n20000_apsp(T, ctx, full_size):
+    """Exact and approximate APSP of the benchmarked TMFG (corr-tmfg P=1) at
+    n=20000, in the benchmark's launch configuration: rows of 48 sampled
+    sources of both matrices equal the oracle's float path-sum rows bit for
+    bit (the approximate rows by the row-sampled oracle of Section 4.3,
+    which still runs the bounded search from every vertex)."""
+    S, Sn = full_size
+    out = T.tmfg_build(ctx, S, "corr", 1)
+    D = T.tmfg_apsp(ctx, S, out["edges"])
     Da = T.tmfg_apsp(ctx, S, out["edges"], approx=True)
     T.tmfg_sync_status(ctx)
-    Das = Da[torch.as_tensor(src, device="cuda:0")].cpu().numpy().astype(np.float64)
-    assert np.array_equal(Das, Da[:, torch.as_tensor(src, device="cuda:0")].T.cpu().numpy())
-    # min over estimates that include the search from t, whose float fold can
-    # end one rounding below the fold from s: compare within float rounding
-    assert np.all(Das >= Dr * (1 - 1e-6))
-    assert np.all(Das[Das < Dr] >= Dr[Das < Dr] * (1 - 1e-6))
+    ref = oracle.tmfg(Sn, "corr", 1)
+    assert np.array_equal(out["edges"].cpu().numpy(), ref["edges"])
+    src_d = torch.as_tensor(FULL_SRC, device="cuda:0")
+    Dr = oracle.sssp_rows(Sn, ref["edges"], FULL_SRC, prec=32)
+    assert np.array_equal(D[src_d].cpu().numpy().astype(np.float64), Dr)
+    Ar = oracle.apsp_approx_rows(Sn, ref["edges"], FULL_SRC, 0, 2.0, prec=32)
+    Das = Da[src_d].cpu().numpy().astype(np.float64)
+    bad = np.argwhere(Das != Ar)
+    assert bad.size == 0, f"{len(bad)} approximate entries differ, first {bad[:3].tolist()}"
+    # the matrix is exactly symmetric (min over both directions)
+    assert np.array_equal(Das, Da[:, src_d].T.cpu().numpy().astype(np.float64))
 
 
 # ------------------------------------------------------------------ host entry point

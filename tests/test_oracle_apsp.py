@@ -166,3 +166,15 @@ def test_sampled_oracle_rows_match_full():
         within = D[s] <= [0.5, 1.0, 2.0][i]
         assert np.array_equal(b[i][within], D[s][within])
     assert np.array_equal(oracle.rowsort_rows(S, [5, 0, 69]), oracle.rowsort(S)[[5, 0, 69]])
+
+
+@pytest.mark.parametrize("seed,n,h,rf,prec", [(13, 90, 0, 2.0, 32), (14, 150, 5, 1.5, 32),
+                                             (15, 120, 0, 3.0, 64), (16, 64, 64, 2.0, 32)])
+def test_approx_rows_match_full_approx(seed, n, h, rf, prec):
+    """The row-sampled approximate APSP (used at sizes where the full n x n
+    oracle does not fit) gives exactly the rows of the full one."""
+    S, edges = tmfg_case(seed, n)
+    D, _ = oracle.apsp_approx(S, edges, h, rf, prec)
+    src = np.array([0, n - 1, n // 2, 7, 7], np.int32)
+    R = oracle.apsp_approx_rows(S, edges, src, h, rf, prec)
+    assert np.array_equal(R, D[src])

@@ -167,3 +167,89 @@ def test_direction_tie_points_to_parent():
     _, info = oracle.dbht(S, t, oracle.apsp_exact(S, t["edges"], 64))
     assert info["direction"].tolist() == [0]
     assert info["converging"].tolist() == [1, 0]
+
+
+GOLDEN_DBHT = os.path.join(os.path.dirname(__file__), "golden", "hand_traced_dbht.json")
+
+
+def load_dbht_case():
+    """The hand-traced DBHT case: S on the TMFG edges (1/64ths), the TMFG
+    itself and an integer distance matrix D, all given explicitly."""
+    case = json.load(open(GOLDEN_DBHT))
+    n = case["n"]
+    S = np.eye(n)
+    for key, val in case["S_edges_64ths"].items():
+        i, j = map(int, key.split(","))
+        S[i, j] = S[j, i] = val / 64.0
+    D = np.zeros((n, n))
+    for key, val in case["D_upper"].items():
+        i, j = map(int, key.split(","))
+        D[i, j] = D[j, i] = float(val)
+    t = {k: np.array(v, np.int32) for k, v in case["tmfg"].items()}
+    return case, S, t, D
+
+
+def test_dbht_assignment_rules_hand_traced():
+    """Rules (d) group of a vertex, (e) home of a bubble and (f) bubble of a
+    vertex of the DBHT reading, each decided once by a margin and once by a
+    tie in the hand trace, and the linkage rows that follow from them."""
+    case, S, t, D = load_dbht_case()
+    Z, info = oracle.dbht(S, t, D)
+    e = case["expect"]
+    assert info["direction"].tolist() == e["direction"]
+    assert info["converging"].tolist() == e["converging"]
+    assert info["group"].tolist() == e["group"]
+    assert info["bubble"].tolist() == e["bubble"]
+    # the home of each bubble shows in which group its vertices landed
+    for v, b in enumerate(e["bubble"]):
+        assert e["home"][b] == e["group"][v]
+    assert Z.tolist() == [[float(x) for x in row] for row in e["linkage"]]
+
+
+def _section(src, marker):
+    """Offset of the code following a comment marker in the oracle source."""
+    i = src.index(marker)
+    return i + len(marker)
+
+
+# Planted mistakes in the assignment rules of oracle_dbht: (marker of the
+# rule's block, text in that block, its replacement).  Each must make the
+# hand-traced case fail.
+DBHT_MUTATIONS = {
+    "d_argmax": ("/* (d) group of each vertex */", "s < bm", "s > bm"),
+    "d_tie_to_larger": ("/* (d) group of each vertex */", "s < bm", "s <= bm"),
+    "e_argmax": ("/* (e) home of each bubble */", "s < bm", "s > bm"),
+    "e_tie_to_larger": ("/* (e) home of each bubble */", "s < bm", "s <= bm"),
+    "f_argmax": ("/* (f) bubble of each vertex */", "s < bm", "s > bm"),
+    "f_tie_to_larger": ("/* (f) bubble of each vertex */", "s < bm", "s <= bm"),
+}
+
+
+@pytest.fixture(scope="module")
+def oracle_source():
+    return open(os.path.join(os.path.dirname(oracle.__file__), "tmfg_oracle.c")).read()
+
+
+def test_unmutated_copy_passes(tmp_path, oracle_source):
+    """Control for the mutation test: an unchanged copy built the same way
+    reproduces the hand trace."""
+    src = tmp_path / "copy.c"
+    src.write_text(oracle_source)
+    lib = oracle.compile_library(str(src), str(tmp_path / "copy.so"))
+    with oracle.use_library(lib):
+        test_dbht_assignment_rules_hand_traced()
+
+
+@pytest.mark.parametrize("name", sorted(DBHT_MUTATIONS))
+def test_planted_assignment_mistake_fails_the_hand_trace(tmp_path, oracle_source, name):
+    marker, old, new = DBHT_MUTATIONS[name]
+    at = _section(oracle_source, marker)
+    k = oracle_source.index(old, at)
+    assert k - at < 1200, "the pattern must lie in the rule's own block"
+    mutated = oracle_source[:k] + new + oracle_source[k + len(old):]
+    src = tmp_path / f"{name}.c"
+    src.write_text(mutated)
+    lib = oracle.compile_library(str(src), str(tmp_path / f"{name}.so"))
+    with oracle.use_library(lib):
+        with pytest.raises(AssertionError):
+            test_dbht_assignment_rules_hand_traced()

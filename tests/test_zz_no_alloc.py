@@ -5,9 +5,10 @@ memory belongs to their own pool or caching allocator, or the calling path
 must not take an allocator's locks and synchronisation).  Its scratch is a
 static device array shared by all calls, so this test calls it twice in a
 row, with different n, and checks each result bit for bit against the
-context-based tmfg_apsp, the tolerance the APSP parity tests use.  It also
-checks the size limit.  Collected last so that a failure here comes after
-every other test has run; it also passes alone in a fresh process.
+context-based tmfg_apsp, the tolerance the APSP parity tests use; a third
+case runs at the largest n the array admits.  It also checks the size
+limit.  Collected last so that a failure here comes after every other test
+has run; it also passes alone in a fresh process.
 """
 import ctypes
 
@@ -18,6 +19,8 @@ from paper_2408_09399_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
+
+NOALLOC_MAX_N = 21581  # TMFG_NOALLOC_MAX_N in include/tmfg.h
 
 
 @pytest.fixture(scope="module")
@@ -35,6 +38,15 @@ def T():
     return T
 
 
+@pytest.fixture
+def ctx(T):
+    c = T.tmfg_create(0)
+    try:
+        yield c
+    finally:
+        c.close()
+
+
 def noalloc(T, S, edges, D, status):
     stream = torch.cuda.current_stream()
     dt = 0 if S.dtype == torch.float32 else 1
@@ -44,24 +56,49 @@ def noalloc(T, S, edges, D, status):
         ctypes.c_void_p(status.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
 
 
-def test_noalloc_matches_context_entry_point_twice(T):
-    ctx = T.tmfg_create(0)
+def device_similarity(n, seed):
+    """A symmetric U(-1, 1) matrix with unit diagonal made on the device
+    (the largest case would take minutes to make on the host)."""
+    g = torch.Generator(device="cuda:0")
+    g.manual_seed(seed)
+    S = torch.rand((n, n), generator=g, device="cuda:0") * 2 - 1
+    S = torch.triu(S, 1)
+    S = S + S.T
+    S.fill_diagonal_(1.0)
+    return S
+
+
+def check_against_context_path(T, ctx, S, mode, status):
+    n = S.shape[0]
+    edges = T.tmfg_build(ctx, S, mode)["edges"]
+    ref = T.tmfg_apsp(ctx, S, edges)
+    T.tmfg_sync_status(ctx)
+    D = torch.full((n, n), float("nan"), dtype=torch.float32, device="cuda:0")
+    assert noalloc(T, S, edges, D, status) == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert torch.equal(D, ref), f"n={n}"
+
+
+def test_noalloc_matches_context_entry_point_twice(T, ctx):
     status = torch.full((1,), -7, dtype=torch.int32, device="cuda:0")
     for n, dtype, seed in [(1500, np.float32, 1), (700, np.float64, 2)]:
         S = torch.as_tensor(W.random_similarity(seed, n, dtype), device="cuda:0")
-        edges = T.tmfg_build(ctx, S, "heap")["edges"]
-        ref = T.tmfg_apsp(ctx, S, edges)
-        T.tmfg_sync_status(ctx)
-        D = torch.full((n, n), float("nan"), dtype=torch.float32, device="cuda:0")
-        assert noalloc(T, S, edges, D, status) == 0
-        torch.cuda.synchronize()
-        assert int(status.item()) == 0
-        assert torch.equal(D, ref), f"n={n}"
-    ctx.close()
+        check_against_context_path(T, ctx, S, "heap", status)
+
+
+def test_noalloc_at_the_largest_size(T, ctx):
+    """The CSR carve at n = TMFG_NOALLOC_MAX_N must fit the static array
+    exactly; a larger exact-path workspace would overrun it."""
+    status = torch.full((1,), -7, dtype=torch.int32, device="cuda:0")
+    S = device_similarity(NOALLOC_MAX_N, 3)
+    check_against_context_path(T, ctx, S, "corr", status)
+    del S
+    torch.cuda.empty_cache()
 
 
 def test_noalloc_rejects_sizes_beyond_the_limit(T):
-    n = 21582  # TMFG_NOALLOC_MAX_N + 1
+    n = NOALLOC_MAX_N + 1
     S = torch.zeros((4, 4), dtype=torch.float32, device="cuda:0")
     edges = torch.zeros((6, 2), dtype=torch.int32, device="cuda:0")
     D = torch.zeros((4, 4), dtype=torch.float32, device="cuda:0")

@@ -66,9 +66,15 @@ int tmfg_create(tmfg_ctx **out, int device, size_t workspace_budget_bytes);
 /* Release the context's device memory.  Synchronises the device first. */
 void tmfg_destroy(tmfg_ctx *ctx);
 
-/* Largest n that tmfg_build supports for `dtype` in this build (the per-row
- * sort keeps one row in shared memory). */
+/* Largest n that tmfg_build supports for `dtype` in this build with
+ * corr-tmfg and prefix 1 (the sorted rows, the loop's per-vertex state and
+ * one APSP distance row each fit one CTA's shared memory; face ids are 16
+ * bits). */
 int64_t tmfg_max_n(int dtype);
+
+/* The same for a given mode and prefix: heap-tmfg and prefixes above 1 keep
+ * more per-vertex state in shared memory and stop at a smaller n. */
+int64_t tmfg_max_n_mode(int dtype, int mode, int prefix);
 
 /* Workspace bytes that tmfg_build (what = 0), tmfg_apsp exact (what = 1)
  * or approximate (what = 2, with n_hubs = 0 meaning ceil(sqrt n)), or
@@ -144,10 +150,31 @@ typedef struct {
     int64_t ldd;
 } tmfg_job;
 
+/* Launch shape of the insertion loop of corr-tmfg with prefix 1 (no paper
+ * counterpart: a tuning knob); 0 fields take the defaults.  Every shape gives
+ * the same TMFG. */
+typedef struct {
+    int32_t threads;       /* threads of the loop's CTA: 256 (default) or 512 */
+    int32_t probe_lanes;   /* lanes per sorted-row refresh: 4, 8 (default) or 16;
+                              with 512 threads 8 or 16 */
+    int32_t stage_groups;  /* index groups of 32 face keys a round copies to
+                              shared memory (default 128; fewer if they do not fit;
+                              -1 = none) */
+    int32_t kernel;        /* 0 = automatic (default: the general loop kernel
+                              where its shared memory holds n, else the prefix-1
+                              kernel), 1 = the prefix-1 loop kernel, 2 = the
+                              general loop kernel that every mode runs */
+} tmfg_loop_shape;
+
+/* Set the loop shape that later tmfg_build and tmfg_solve_host calls on this
+ * context use (NULL = defaults).  TMFG_EINVAL for an unsupported shape. */
+int tmfg_set_loop_shape(tmfg_ctx *ctx, const tmfg_loop_shape *shape);
+
 /* Launch shapes of a batched run; 0 fields take the defaults.  Chosen by an
  * autotuner on the Python side (paper_2408_09399_gb300.autotune). */
 typedef struct {
     int32_t sssp_threads;   /* threads per search CTA: 256 or 512 (default) */
+    tmfg_loop_shape loop;   /* the loop's shape (corr-tmfg, prefix 1) */
 } tmfg_batch_config;
 
 /* Many TMFG constructions (and optionally exact APSPs) in one launch per

@@ -47,8 +47,13 @@ class _Job(ctypes.Structure):
                 ("D", ctypes.c_void_p), ("ldd", ctypes.c_int64)]
 
 
+class _LoopShape(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("probe_lanes", ctypes.c_int32),
+                ("stage_groups", ctypes.c_int32), ("kernel", ctypes.c_int32)]
+
+
 class _BatchConfig(ctypes.Structure):
-    _fields_ = [("sssp_threads", ctypes.c_int32)]
+    _fields_ = [("sssp_threads", ctypes.c_int32), ("loop", _LoopShape)]
 
 
 class _DbhtOutputs(ctypes.Structure):
@@ -96,6 +101,8 @@ def load_library():
         lib.tmfg_destroy.restype = None
         lib.tmfg_max_n.argtypes = [ctypes.c_int]
         lib.tmfg_max_n.restype = i64
+        lib.tmfg_max_n_mode.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        lib.tmfg_max_n_mode.restype = i64
         lib.tmfg_workspace_bytes.argtypes = [i64, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.tmfg_workspace_bytes.restype = ctypes.c_size_t
         lib.tmfg_build.argtypes = [P, P, i64, i64, ctypes.POINTER(_Params), P, P, P, P, P]
@@ -107,6 +114,8 @@ def load_library():
         lib.tmfg_batch_run.argtypes = [P, ctypes.POINTER(_Job), ctypes.c_int32,
                                        ctypes.POINTER(_Params), ctypes.POINTER(_BatchConfig), P]
         lib.tmfg_batch_run.restype = ctypes.c_int
+        lib.tmfg_set_loop_shape.argtypes = [P, ctypes.POINTER(_LoopShape)]
+        lib.tmfg_set_loop_shape.restype = ctypes.c_int
         lib.dbht_cluster.argtypes = [P, P, i64, i64, i32, P, P, P, P, P, i64, P, P]
         lib.dbht_cluster.restype = ctypes.c_int
         lib.dbht_cluster_detail.argtypes = [P, P, i64, i64, i32, P, P, P, P, P, i64, P,
@@ -224,8 +233,10 @@ def tmfg_destroy(ctx: Context):
     ctx.close()
 
 
-def tmfg_max_n(dtype: int = TMFG_F32) -> int:
-    return int(load_library().tmfg_max_n(int(dtype)))
+def tmfg_max_n(dtype: int = TMFG_F32, mode: str = "corr", prefix: int = 1) -> int:
+    """Largest n tmfg_build takes for this dtype, mode and prefix."""
+    m = {"corr": TMFG_CORR, "heap": TMFG_HEAP}[mode]
+    return int(load_library().tmfg_max_n_mode(int(dtype), m, int(prefix)))
 
 
 def tmfg_workspace_bytes(n: int, dtype: int = TMFG_F32, what: int = 0, n_hubs: int = 0) -> int:
@@ -401,8 +412,24 @@ def dbht_cluster_detail(ctx: Context, S, t, D, linkage=None, stream=None):
     return linkage, info
 
 
+def _loop_shape(shape) -> "_LoopShape":
+    shape = shape or {}
+    return _LoopShape(int(shape.get("threads", 0)), int(shape.get("probe_lanes", 0)),
+                      int(shape.get("stage_groups", 0)), int(shape.get("kernel", 0)))
+
+
+def tmfg_set_loop_shape(ctx: Context, shape=None) -> None:
+    """Shape of the corr-tmfg prefix-1 insertion loop for this context's later
+    builds: a dict with threads (256/512), probe_lanes (4/8/16),
+    stage_groups (0 default, -1 none) and kernel (0 automatic, 1 the prefix-1
+    kernel, 2 the general one); None restores the defaults.  Every shape
+    gives the same TMFG."""
+    _check(load_library().tmfg_set_loop_shape(ctx.handle, ctypes.byref(_loop_shape(shape))),
+           "tmfg_set_loop_shape")
+
+
 def tmfg_batch_run(ctx: Context, mats, mode: str = "corr", prefix: int = 1, apsp: bool = True,
-                   sssp_threads: int = 0, outs=None, stream=None):
+                   sssp_threads: int = 0, outs=None, stream=None, loop_shape=None):
     """TMFG (and exact APSP when ``apsp``) of every matrix in ``mats`` (CUDA
     tensors of one dtype) with one launch per stage.  Returns a list of dicts
     like tmfg_build's, plus "D" when ``apsp``.  Asynchronous."""
@@ -431,7 +458,7 @@ def tmfg_batch_run(ctx: Context, mats, mode: str = "corr", prefix: int = 1, apsp
                        o["ins_face"].data_ptr(), o["bubble_parent"].data_ptr(),
                        D.data_ptr() if D is not None else None, D.stride(0) if D is not None else 0)
     p = _Params({"corr": TMFG_CORR, "heap": TMFG_HEAP}[mode], int(prefix), dt, 0)
-    cfg = _BatchConfig(int(sssp_threads))
+    cfg = _BatchConfig(int(sssp_threads), _loop_shape(loop_shape))
     rc = load_library().tmfg_batch_run(ctx.handle, jobs, len(mats), ctypes.byref(p),
                                        ctypes.byref(cfg), _stream_handle(stream))
     _check(rc, "tmfg_batch_run")

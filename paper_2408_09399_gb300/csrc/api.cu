@@ -198,7 +198,7 @@ int launch_build_loop(tmfg_ctx *ctx, const BuildWork &w, const void *S, int64_t 
     a.status = ctx->status;
     a.stats = ctx->stats;
     a.timeout_ns = ctx->timeout_ns;
-    return launch_loop(a, dtype, st);
+    return launch_loop(a, dtype, st, ctx->loop_shape);
 }
 
 // The device block of tmfg_solve_host (grown like the workspace).
@@ -291,16 +291,18 @@ void tmfg_destroy(tmfg_ctx *ctx)
     delete ctx;
 }
 
-int64_t tmfg_max_n(int dtype)
+int64_t tmfg_max_n_mode(int dtype, int mode, int prefix)
 {
     if (dtype != TMFG_F32 && dtype != TMFG_F64) return 0;
+    if (mode != TMFG_CORR && mode != TMFG_HEAP) return 0;
     int64_t m = rowsort_max_n(dtype);
-    while (m > 4 && (loop_smem_bytes((int)m, dtype, TMFG_HEAP) > kSmemLimit ||
-                      loop_smem_bytes((int)m, dtype, TMFG_CORR) > kSmemLimit ||
-                      sssp_smem_bytes((int)m) > kSmemLimit || 2 * m - 4 > 65535))
-        --m;
+    const int64_t lm = loop_max_n(dtype, mode, prefix > 1 ? 2 : 1);
+    if (lm < m) m = lm;
+    while (m > 4 && (sssp_smem_bytes((int)m) > kSmemLimit || 2 * m - 4 > 65535)) --m;
     return m;
 }
+
+int64_t tmfg_max_n(int dtype) { return tmfg_max_n_mode(dtype, TMFG_CORR, 1); }
 
 size_t tmfg_workspace_bytes(int64_t n, int dtype, int what, int n_hubs)
 {
@@ -335,7 +337,7 @@ int tmfg_build(tmfg_ctx *ctx, const void *S, int64_t n, int64_t ld, const tmfg_p
     if (params->mode != TMFG_CORR && params->mode != TMFG_HEAP) return TMFG_EINVAL;
     if (params->prefix < 1 || params->prefix > kMaxPrefixApi) return TMFG_EINVAL;
     if (params->mode == TMFG_HEAP && params->prefix != 1) return TMFG_EINVAL;
-    if (n > tmfg_max_n(dtype)) return TMFG_ETOOBIG;
+    if (n > tmfg_max_n_mode(dtype, params->mode, params->prefix)) return TMFG_ETOOBIG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return TMFG_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -365,7 +367,9 @@ int tmfg_batch_run(tmfg_ctx *ctx, const tmfg_job *jobs, int32_t count, const tmf
     if (params->mode == TMFG_HEAP && params->prefix != 1) return TMFG_EINVAL;
     const int sssp_threads = (cfg && cfg->sssp_threads) ? cfg->sssp_threads : 512;
     if (sssp_threads != 256 && sssp_threads != 512) return TMFG_EINVAL;
-    const int64_t maxn_lib = tmfg_max_n(dtype);
+    LoopShape shape;
+    if (!loop_shape_from(cfg ? &cfg->loop : nullptr, &shape)) return TMFG_EINVAL;
+    const int64_t maxn_lib = tmfg_max_n_mode(dtype, params->mode, params->prefix);
     int max_n = 0, napsp = 0;
     for (int i = 0; i < count; ++i) {
         const tmfg_job &J = jobs[i];
@@ -537,7 +541,7 @@ int tmfg_batch_run(tmfg_ctx *ctx, const tmfg_job *jobs, int32_t count, const tmf
     rc = launch_rowsort_batch(d_sort, d_rows, count, max_n, dtype, ctx->status,
                               ctx->num_sms * 2, st);
     if (rc) return rc;
-    rc = launch_loop_batch(d_loop, count, max_n, dtype, params->mode, st);
+    rc = launch_loop_batch(d_loop, count, max_n, dtype, params->mode, params->prefix, st, shape);
     if (rc) return rc;
     if (napsp)
         rc = launch_apsp_batch(d_ajob, d_sarg, d_ebeg, d_sbeg, napsp, edge_acc, max_n, dtype,
@@ -625,7 +629,7 @@ int tmfg_solve_host(tmfg_ctx *ctx, const void *S_host, int64_t n, int64_t ld,
     if (params->mode != TMFG_CORR && params->mode != TMFG_HEAP) return TMFG_EINVAL;
     if (params->prefix < 1 || params->prefix > kMaxPrefixApi) return TMFG_EINVAL;
     if (params->mode == TMFG_HEAP && params->prefix != 1) return TMFG_EINVAL;
-    if (n > tmfg_max_n(dtype)) return TMFG_ETOOBIG;
+    if (n > tmfg_max_n_mode(dtype, params->mode, params->prefix)) return TMFG_ETOOBIG;
     const int h = hubs_for(n, sp ? sp->n_hubs : 0);
     const float rf = (sp && sp->radius_factor > 0.0f) ? sp->radius_factor : 2.0f;
     if (D_approx && (h < 1 || 4 * (n + h) > (int64_t)kSmemLimit - 1024)) return TMFG_EINVAL;
@@ -759,6 +763,15 @@ int tmfg_sync_status(tmfg_ctx *ctx, void *stream)
         return TMFG_ECUDA;
     if (code && cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess) return TMFG_ECUDA;
     return code;
+}
+
+int tmfg_set_loop_shape(tmfg_ctx *ctx, const tmfg_loop_shape *shape)
+{
+    if (!ctx) return TMFG_EINVAL;
+    LoopShape s;
+    if (!loop_shape_from(shape, &s)) return TMFG_EINVAL;
+    ctx->loop_shape = s;
+    return TMFG_OK;
 }
 
 int tmfg_last_stats(tmfg_ctx *ctx, int64_t *out, int count)

@@ -13,6 +13,7 @@ struct tmfg_ctx {
     int *status;        // device word
     long long *stats;   // device [8]
     long long host_stats[16];
+    tmfg::LoopShape loop_shape;  // shape of the corr-tmfg prefix-1 loop (tmfg_set_loop_shape)
     unsigned long long timeout_ns;
     void *stage;          // pinned host staging buffer for batch descriptor tables
     size_t stage_bytes;

@@ -55,11 +55,44 @@ struct LoopArgs {
     int k_stop;                   // a segment stops once k >= k_stop
     int resume;                   // 0: first segment; 1: continue from state
 };
+// Launch shape of the corr-tmfg prefix-1 loop kernel (loop_corr1.cu):
+// threads per CTA (256 or 512), lanes per sorted-row refresh (4, 8 or 16;
+// 512 threads: 8 or 16), and the index groups whose keys a round copies to
+// shared memory (fewer when the shared memory does not hold them).
+struct LoopShape {
+    int threads = 256;
+    int lanes = 8;
+    int groups = 128;
+    // which kernel runs corr-tmfg prefix 1: -1 automatic (the general kernel
+    // where its shared memory holds n, else the prefix-1 kernel), 0 the
+    // prefix-1 kernel, 1 the general kernel
+    int general = -1;
+};
+// LoopShape from the ABI's tmfg_loop_shape (NULL or 0 fields: defaults);
+// false for an unsupported shape
+bool loop_shape_from(const tmfg_loop_shape *in, LoopShape *out);
 size_t loop_smem_bytes(int n, int dtype, int mode);
 size_t loop_state_bytes(int n);
-int launch_loop(const LoopArgs &args, int dtype, cudaStream_t stream);
-int launch_loop_batch(const LoopArgs *d_args, int count, int max_n, int dtype, int mode,
-                      cudaStream_t stream);
+int launch_loop(const LoopArgs &args, int dtype, cudaStream_t stream,
+                const LoopShape &shape = LoopShape{});
+int launch_loop_batch(const LoopArgs *d_args, int count, int max_n, int dtype, int mode, int P,
+                      cudaStream_t stream, const LoopShape &shape = LoopShape{});
+// the smallest shared-memory carve-out (percent) that holds `ctas` CTAs of
+// `smem` dynamic bytes each
+int carveout_percent(size_t smem, int ctas);
+
+// loop_corr1.cu
+// gp: the layout whose row pointers live in global memory (large n)
+size_t corr1_smem_bytes(int n, int dtype, int groups, bool gp);
+// the copy groups (at most `want`) that fit `limit` bytes, or -1 if nothing fits
+int corr1_fit_groups(int n, int dtype, int want, size_t limit, bool gp);
+bool corr1_shape_ok(int threads, int lanes);
+int launch_corr1(const LoopArgs &a, const LoopShape &shape, int dtype, size_t smem, bool gp,
+                 cudaStream_t stream);
+// the largest n the loop of (mode, prefix) holds, for dtype
+int64_t loop_max_n(int dtype, int mode, int prefix);
+int launch_corr1_batch(const LoopArgs *d_args, int count, const LoopShape &shape, int dtype,
+                       size_t smem, cudaStream_t stream);
 
 // apsp.cu
 struct SsspArgs {

@@ -172,18 +172,16 @@ __device__ __forceinline__ void store_row(const uint16_t *pos, int m, int v, uin
     }
 }
 
-// ---------------------------------------------------------------- float rows
-// Sort row v of an n x n float matrix (row = S + v*ld) into out (ldi ids).
+// ------------------------------------------------------- 32-bit key radix
+// Stable sort of m 32-bit keys (key0, at smem + kHistBytes + 256) in four
+// 8-bit passes; the key shrinks by a byte per pass and is packed with the
+// 16-bit position, so the buffers take 10 bytes per entry.  Leaves the sorted
+// positions in out16 (the start of the same region).
 template <int I>
-__device__ __forceinline__ void sort_row_f32(const float *__restrict__ row, int n, int v,
-                                             bool vec_in, uint16_t *__restrict__ out,
-                                             long long ldi, bool vec_out, long long *rowsum_v,
-                                             int *status, unsigned char *smem)
+__device__ __forceinline__ void radix_key32(int m, unsigned char *smem)
 {
-    const int m = n - 1;
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
     uint32_t *wsum = reinterpret_cast<uint32_t *>(smem + kHistBytes);
-    long long *red = reinterpret_cast<long long *>(smem + kHistBytes + 64);
     unsigned char *r1 = smem + kHistBytes + 256;  // 4m bytes: KEY0, then P2, then OUT16
     const int r1_bytes = ((4 * m + 15) / 16) * 16;
     unsigned char *r2 = r1 + r1_bytes;            // 6m bytes: P1 (key24 + pos), then P3
@@ -193,6 +191,64 @@ __device__ __forceinline__ void sort_row_f32(const float *__restrict__ row, int 
     uint32_t *p1k = reinterpret_cast<uint32_t *>(r2);
     uint16_t *p1v = reinterpret_cast<uint16_t *>(r2 + 4 * (size_t)m);
     uint32_t *p3 = reinterpret_cast<uint32_t *>(r2);
+    radix_pass<I>(m, hist, wsum,
+        [&](int p) { return key0[p] & 0xFFu; },
+        [&](int p, uint32_t q) { p1k[q] = key0[p] >> 8; p1v[q] = (uint16_t)p; });
+    radix_pass<I>(m, hist, wsum,
+        [&](int p) { return p1k[p] & 0xFFu; },
+        [&](int p, uint32_t q) { p2[q] = ((p1k[p] >> 8) << 16) | p1v[p]; });
+    radix_pass<I>(m, hist, wsum,
+        [&](int p) { return (p2[p] >> 16) & 0xFFu; },
+        [&](int p, uint32_t q) { p3[q] = ((p2[p] >> 24) << 16) | (p2[p] & 0xFFFFu); });
+    radix_pass<I>(m, hist, wsum,
+        [&](int p) { return p3[p] >> 16; },
+        [&](int p, uint32_t q) { out16[q] = (uint16_t)(p3[p] & 0xFFFFu); });
+}
+
+// ------------------------------------------------------- 64-bit key radix
+// Stable sort of m 64-bit keys (k0 at smem + kHistBytes + 256, then k1, v0,
+// v1: 20 bytes per entry) in eight 8-bit passes; leaves the sorted positions
+// in v0 (returned).
+template <int I>
+__device__ __forceinline__ uint16_t *radix_key64(int m, unsigned char *smem)
+{
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *wsum = reinterpret_cast<uint32_t *>(smem + kHistBytes);
+    unsigned char *base = smem + kHistBytes + 256;
+    uint64_t *k0 = reinterpret_cast<uint64_t *>(base);
+    uint64_t *k1 = k0 + m;
+    uint16_t *v0 = reinterpret_cast<uint16_t *>(k1 + m);
+    uint16_t *v1 = v0 + m;
+    // pass 0: positions are implicit
+    radix_pass<I>(m, hist, wsum,
+        [&](int p) { return (uint32_t)(k0[p] & 0xFFu); },
+        [&](int p, uint32_t q) { k1[q] = k0[p]; v1[q] = (uint16_t)p; });
+#pragma unroll 1
+    for (int pass = 1; pass < 8; ++pass) {
+        const int sh = 8 * pass;
+        uint64_t *ks = (pass & 1) ? k1 : k0;
+        uint64_t *kd = (pass & 1) ? k0 : k1;
+        uint16_t *vs = (pass & 1) ? v1 : v0;
+        uint16_t *vd = (pass & 1) ? v0 : v1;
+        radix_pass<I>(m, hist, wsum,
+            [&](int p) { return (uint32_t)((ks[p] >> sh) & 0xFFu); },
+            [&](int p, uint32_t q) { kd[q] = ks[p]; vd[q] = vs[p]; });
+    }
+    return v0;  // after 8 passes the result is in (k0, v0)
+}
+
+// ---------------------------------------------------------------- float rows
+// Sort row v of an n x n float matrix (row = S + v*ld) into out (ldi ids).
+template <int I>
+__device__ __forceinline__ void sort_row_f32(const float *__restrict__ row, int n, int v,
+                                             bool vec_in, uint16_t *__restrict__ out,
+                                             long long ldi, bool vec_out, long long *rowsum_v,
+                                             int *status, unsigned char *smem)
+{
+    const int m = n - 1;
+    long long *red = reinterpret_cast<long long *>(smem + kHistBytes + 64);
+    uint32_t *key0 = reinterpret_cast<uint32_t *>(smem + kHistBytes + 256);
+    const uint16_t *out16 = reinterpret_cast<const uint16_t *>(smem + kHistBytes + 256);
 
     long long acc = 0;
     int bad = 0;
@@ -223,19 +279,7 @@ __device__ __forceinline__ void sort_row_f32(const float *__restrict__ row, int 
     const long long rs = block_sum_ll(acc, red);
     if (threadIdx.x == 0 && rowsum_v) *rowsum_v = rs;
 
-    radix_pass<I>(m, hist, wsum,
-        [&](int p) { return key0[p] & 0xFFu; },
-        [&](int p, uint32_t q) { p1k[q] = key0[p] >> 8; p1v[q] = (uint16_t)p; });
-    radix_pass<I>(m, hist, wsum,
-        [&](int p) { return p1k[p] & 0xFFu; },
-        [&](int p, uint32_t q) { p2[q] = ((p1k[p] >> 8) << 16) | p1v[p]; });
-    radix_pass<I>(m, hist, wsum,
-        [&](int p) { return (p2[p] >> 16) & 0xFFu; },
-        [&](int p, uint32_t q) { p3[q] = ((p2[p] >> 24) << 16) | (p2[p] & 0xFFFFu); });
-    radix_pass<I>(m, hist, wsum,
-        [&](int p) { return p3[p] >> 16; },
-        [&](int p, uint32_t q) { out16[q] = (uint16_t)(p3[p] & 0xFFFFu); });
-
+    radix_key32<I>(m, smem);
     store_row(out16, m, v, out, ldi, vec_out);
     __syncthreads();
 }
@@ -248,14 +292,8 @@ __device__ __forceinline__ void sort_row_f64(const double *__restrict__ row, int
                                              int *status, unsigned char *smem)
 {
     const int m = n - 1;
-    uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
-    uint32_t *wsum = reinterpret_cast<uint32_t *>(smem + kHistBytes);
     long long *red = reinterpret_cast<long long *>(smem + kHistBytes + 64);
-    unsigned char *base = smem + kHistBytes + 256;
-    uint64_t *k0 = reinterpret_cast<uint64_t *>(base);
-    uint64_t *k1 = k0 + m;
-    uint16_t *v0 = reinterpret_cast<uint16_t *>(k1 + m);
-    uint16_t *v1 = v0 + m;
+    uint64_t *k0 = reinterpret_cast<uint64_t *>(smem + kHistBytes + 256);
 
     long long acc = 0;
     int bad = 0;
@@ -284,23 +322,8 @@ __device__ __forceinline__ void sort_row_f64(const double *__restrict__ row, int
     const long long rs = block_sum_ll(acc, red);
     if (threadIdx.x == 0 && rowsum_v) *rowsum_v = rs;
 
-    // pass 0: positions are implicit
-    radix_pass<I>(m, hist, wsum,
-        [&](int p) { return (uint32_t)(k0[p] & 0xFFu); },
-        [&](int p, uint32_t q) { k1[q] = k0[p]; v1[q] = (uint16_t)p; });
-#pragma unroll 1
-    for (int pass = 1; pass < 8; ++pass) {
-        const int sh = 8 * pass;
-        uint64_t *ks = (pass & 1) ? k1 : k0;
-        uint64_t *kd = (pass & 1) ? k0 : k1;
-        uint16_t *vs = (pass & 1) ? v1 : v0;
-        uint16_t *vd = (pass & 1) ? v0 : v1;
-        radix_pass<I>(m, hist, wsum,
-            [&](int p) { return (uint32_t)((ks[p] >> sh) & 0xFFu); },
-            [&](int p, uint32_t q) { kd[q] = ks[p]; vd[q] = vs[p]; });
-    }
-    // after 8 passes the result is in (k0, v0)
-    store_row(v0, m, v, out, ldi, vec_out && ((uintptr_t)v0 % 16 == 0));
+    const uint16_t *sorted = radix_key64<I>(m, smem);
+    store_row(sorted, m, v, out, ldi, vec_out && ((uintptr_t)sorted % 16 == 0));
     __syncthreads();
 }
 
@@ -313,6 +336,112 @@ __device__ __forceinline__ void sort_row(const T *row, int n, int v, bool vec_in
         sort_row_f32<I>(row, n, v, vec_in, out, ldi, vec_out, rowsum_v, status, smem);
     else
         sort_row_f64<I>(row, n, v, vec_in, out, ldi, vec_out, rowsum_v, status, smem);
+}
+
+// ------------------------------------------------------------ long rows
+// A row longer than one CTA's shared memory sorts in three steps: the
+// positions [0, h) and [h, m) (h = ceil(m / 2)) are each sorted as above
+// and their ids written to the output row; then the whole row is read again
+// (with the exact sum and the entry checks), its keys kept in shared memory
+// by position, and the two sorted halves are merged by merge path.  Every
+// id of the first half is smaller than every id of the second, so taking
+// the first half's entry on equal keys keeps the (S desc, u asc) order.
+
+template <typename T>
+using key_of_t = std::conditional_t<sizeof(T) == 4, uint32_t, uint64_t>;
+
+// Sort positions [p0, p0 + cnt) of row v by key (ties in position order);
+// ids to out[p0 + j].
+template <int I, typename T>
+__device__ __forceinline__ void sort_part(const T *__restrict__ row, int v, int p0, int cnt,
+                                          uint16_t *__restrict__ out, unsigned char *smem)
+{
+    using K = key_of_t<T>;
+    K *key0 = reinterpret_cast<K *>(smem + kHistBytes + 256);
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+        const int p = p0 + j;
+        const int u = p + (p >= v);
+        key0[j] = ~ord_key(canon(row[u]));
+    }
+    __syncthreads();
+    const uint16_t *sorted;
+    if constexpr (sizeof(T) == 4) {
+        radix_key32<I>(cnt, smem);
+        sorted = reinterpret_cast<const uint16_t *>(smem + kHistBytes + 256);
+    } else {
+        sorted = radix_key64<I>(cnt, smem);
+    }
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+        const int p = p0 + sorted[j];
+        out[p0 + j] = (uint16_t)(p + (p >= v));
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void merge_halves(const T *__restrict__ row, int n, int v,
+                                             uint16_t *__restrict__ out, long long ldi,
+                                             long long *rowsum_v, int *status,
+                                             unsigned char *smem)
+{
+    using K = key_of_t<T>;
+    const int m = n - 1, na = (m + 1) / 2, nb = m - na;
+    long long *red = reinterpret_cast<long long *>(smem + kHistBytes + 64);
+    K *key = reinterpret_cast<K *>(smem + kHistBytes + 256);
+    uint16_t *ids = reinterpret_cast<uint16_t *>(key + m);
+    long long acc = 0;
+    int bad = 0;
+    for (int u = threadIdx.x; u < n; u += blockDim.x) {
+        if (u == v) continue;
+        const T x = canon(row[u]);
+        const int c = check_entry(x);
+        if (c) bad = c;
+        acc += quantize40(x);
+        key[u - (u > v)] = ~ord_key(x);
+    }
+    for (int j = threadIdx.x; j < m; j += blockDim.x) ids[j] = out[j];
+    if (bad) set_status(status, bad);
+    __syncthreads();
+    const long long rs = block_sum_ll(acc, red);
+    if (threadIdx.x == 0 && rowsum_v) *rowsum_v = rs;
+    const uint16_t *A = ids, *B = ids + na;
+    auto kof = [&](int id) { return key[id - (id > v)]; };
+    const int per = (m + blockDim.x - 1) / blockDim.x;
+    const int d0 = threadIdx.x * per;
+    if (d0 < m) {
+        const int d1 = d0 + per < m ? d0 + per : m;
+        // merge path: i = the number of first-half entries among the first d0
+        int lo = d0 > nb ? d0 - nb : 0, hi = d0 < na ? d0 : na;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (kof(A[mid]) <= kof(B[d0 - mid - 1])) lo = mid + 1;
+            else hi = mid;
+        }
+        int i = lo, j = d0 - lo;
+        for (int d = d0; d < d1; ++d) {
+            const bool takeA = j >= nb || (i < na && kof(A[i]) <= kof(B[j]));
+            out[d] = takeA ? A[i++] : B[j++];
+        }
+    }
+    for (int j = m + threadIdx.x; j < ldi; j += blockDim.x) out[j] = kNone16;
+    __syncthreads();
+}
+
+template <int I, typename T>
+__global__ void __launch_bounds__(kSortThreads, 1)
+rowsort_long_kernel(const T *__restrict__ S, int n, long long ld, uint16_t *__restrict__ idx,
+                    long long ldi, long long *__restrict__ rowsum, int *status, int row0,
+                    int row1)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int m = n - 1, na = (m + 1) / 2;
+    for (int v = row0 + blockIdx.x; v < row1; v += gridDim.x) {
+        const T *row = S + (long long)v * ld;
+        uint16_t *out = idx + (long long)v * ldi;
+        sort_part<I, T>(row, v, 0, na, out, smem);
+        sort_part<I, T>(row, v, na, m - na, out, smem);
+        merge_halves<T>(row, n, v, out, ldi, rowsum ? rowsum + v : nullptr, status, smem);
+    }
 }
 
 // One matrix: a persistent grid walks its rows.
@@ -364,22 +493,37 @@ static int pick_items(int m, int dtype)
     return -1;
 }
 
-int64_t rowsort_max_n(int dtype)
-{
-    // largest n whose row fits in shared memory and in the largest I
-    if (dtype == TMFG_F32) {
-        int m = (kSortSmemMax - kHistBytes - 256 - 64) / 10;
-        m = m < 43 * kSortThreads ? m : 43 * kSortThreads;
-        return m + 1;
-    }
-    int m = (kSortSmemMax - kHistBytes - 256 - 64) / 20;
-    m = m < 22 * kSortThreads ? m : 22 * kSortThreads;
-    return m + 1;
-}
-
+// Shared memory of the one-pass sort of a row of n, and of the long-row
+// sort (two halves, then the merge).
 size_t rowsort_smem(int n, int dtype)
 {
     return dtype == TMFG_F32 ? (size_t)sort_smem_f32(n - 1) : (size_t)sort_smem_f64(n - 1);
+}
+
+static size_t rowsort_long_smem(int n, int dtype)
+{
+    const size_t m = (size_t)n - 1, na = (m + 1) / 2;
+    const size_t part = dtype == TMFG_F32 ? ((4 * na + 15) / 16) * 16 + 6 * na : 20 * na;
+    const size_t merge = dtype == TMFG_F32 ? 6 * m : 10 * m;
+    return kHistBytes + 256 + (part > merge ? part : merge) + 64;
+}
+
+static bool rowsort_fits(int n, int dtype)
+{
+    return pick_items(n - 1, dtype) > 0 && rowsort_smem(n, dtype) <= (size_t)kSortSmemMax;
+}
+
+static bool rowsort_long_fits(int n, int dtype)
+{
+    return pick_items(n / 2, dtype) > 0 && rowsort_long_smem(n, dtype) <= (size_t)kSortSmemMax;
+}
+
+int64_t rowsort_max_n(int dtype)
+{
+    // the largest n that one of the two paths sorts (ids are 16 bits)
+    int n = 65535;
+    while (n > 2 && !rowsort_fits(n, dtype) && !rowsort_long_fits(n, dtype)) --n;
+    return n;
 }
 
 // Launch one kernel instance K<I, T> for the items count I (a switch over
@@ -415,14 +559,27 @@ static int launch_rowsort_t(const void *S, int n, long long ld, uint16_t *idx, l
                             cudaStream_t stream)
 {
     const int dtype = sizeof(T) == 4 ? TMFG_F32 : TMFG_F64;
-    const int I = pick_items(n - 1, dtype);
-    const size_t smem = rowsort_smem(n, dtype);
-    if (I < 0 || smem > (size_t)kSortSmemMax) return TMFG_ETOOBIG;
-    const bool vec_out = (ldi % 8 == 0) && ((uintptr_t)idx % 16 == 0);
-    const bool vec_in = (ld % (16 / sizeof(T)) == 0) && ((uintptr_t)S % 16 == 0);
     const int rows = row1 - row0;
     if (rows <= 0) return TMFG_OK;
     const int grid = rows < num_sms ? rows : num_sms;
+    if (!rowsort_fits(n, dtype)) {
+        if (!rowsort_long_fits(n, dtype)) return TMFG_ETOOBIG;
+        const size_t smem = rowsort_long_smem(n, dtype);
+        return dispatch_items<T>(pick_items((n - 1 + 1) / 2, dtype), [&](auto ic) {
+            constexpr int II = decltype(ic)::value;
+            auto k = rowsort_long_kernel<II, T>;
+            if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess)
+                return (int)TMFG_ECUDA;
+            k<<<grid, kSortThreads, smem, stream>>>(static_cast<const T *>(S), n, ld, idx, ldi,
+                                                     rowsum, status, row0, row1);
+            return cudaGetLastError() == cudaSuccess ? (int)TMFG_OK : (int)TMFG_ECUDA;
+        });
+    }
+    const int I = pick_items(n - 1, dtype);
+    const size_t smem = rowsort_smem(n, dtype);
+    const bool vec_out = (ldi % 8 == 0) && ((uintptr_t)idx % 16 == 0);
+    const bool vec_in = (ld % (16 / sizeof(T)) == 0) && ((uintptr_t)S % 16 == 0);
     return dispatch_items<T>(I, [&](auto ic) {
         constexpr int II = decltype(ic)::value;
         auto k = rowsort_kernel<II, T>;
@@ -450,9 +607,10 @@ int launch_rowsort(const void *S, int n, long long ld, int dtype, uint16_t *idx,
 int launch_rowsort_batch(const SortJob *d_jobs, const int *d_row_begin, int njobs, int max_n,
                          int dtype, int *status, int grid, cudaStream_t stream)
 {
+    // the batched sort keeps every row in one pass (the serving sizes)
+    if (!rowsort_fits(max_n, dtype)) return TMFG_ETOOBIG;
     const int I = pick_items(max_n - 1, dtype);
     const size_t smem = rowsort_smem(max_n, dtype);
-    if (I < 0 || smem > (size_t)kSortSmemMax) return TMFG_ETOOBIG;
     auto go = [&](auto tag) {
         using T = decltype(tag);
         return dispatch_items<T>(I, [&](auto ic) {

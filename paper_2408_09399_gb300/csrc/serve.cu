@@ -294,7 +294,7 @@ int64_t tmfg_serve_submit(tmfg_server *s, const tmfg_job *job, void *stream)
     if (!J.S || J.n < 4 || J.ld < J.n || !J.order || !J.edges || !J.bubble_parent ||
         (J.n > 4 && !J.ins_face) || (J.D && J.ldd < J.n) || (s->cfg.apsp && !J.D))
         return -TMFG_EINVAL;
-    if (J.n > tmfg_max_n(s->params.dtype)) return -TMFG_ETOOBIG;
+    if (J.n > tmfg_max_n_mode(s->params.dtype, s->params.mode, s->params.prefix)) return -TMFG_ETOOBIG;
     Request r{};
     r.job = J;
     if (!s->cfg.apsp) r.job.D = nullptr;

@@ -576,7 +576,7 @@ __device__ __forceinline__ void loop_body(const LoopArgs &a)
     __shared__ long long s_red_r[kLoopWarps];
     __shared__ int s_red_i[kLoopWarps];
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const int n = a.n;
     if (*(volatile int *)a.status != 0) return;  // an earlier step failed
     const uint64_t t0 = globaltimer_ns();
@@ -1238,23 +1238,68 @@ int carveout_percent(size_t smem, int ctas)
     return pct > 100 ? 100 : (int)pct;
 }
 
+bool loop_shape_from(const tmfg_loop_shape *in, LoopShape *out)
+{
+    LoopShape s;
+    if (in) {
+        if (in->threads) s.threads = in->threads;
+        if (in->probe_lanes) s.lanes = in->probe_lanes;
+        if (in->stage_groups > 0) s.groups = in->stage_groups;
+        if (in->stage_groups < 0) s.groups = 0;
+        if (in->kernel < 0 || in->kernel > 2) return false;
+        s.general = in->kernel - 1;
+    }
+    if (!corr1_shape_ok(s.threads, s.lanes)) return false;
+    *out = s;
+    return true;
+}
+
 // The insertion loop runs in segments; between them every sorted row is
 // compacted to its uninserted ids, so the lazy pointers keep finding an
 // uninserted id in their first probe.  Segments end after 1/2, 3/4, 7/8,
-// 15/16, 31/32 of the insertions (for n >= 1024).
-int launch_loop(const LoopArgs &args, int dtype, cudaStream_t stream)
+// 15/16, 31/32 of the insertions (for n >= 1024).  corr-tmfg with prefix 1
+// runs on its own kernel (loop_corr1.cu), every other mode on this file's.
+int64_t loop_max_n(int dtype, int mode, int prefix)
 {
-    const size_t smem = loop_smem_bytes(args.n, dtype, args.mode);
-    if (smem > kSmemLimit || 2 * (size_t)args.n - 4 > 65535) return TMFG_ETOOBIG;
+    int64_t m = 32769;  // 2n - 4 face ids in 16 bits
+    if (mode == TMFG_CORR && prefix == 1) {
+        while (m > 4 && corr1_fit_groups((int)m, dtype, 0, kSmemLimit, true) < 0) --m;
+        return m;
+    }
+    while (m > 4 && loop_smem_bytes((int)m, dtype, mode) > kSmemLimit) --m;
+    return m;
+}
+
+int launch_loop(const LoopArgs &args, int dtype, cudaStream_t stream, const LoopShape &shape)
+{
+    if (2 * (size_t)args.n - 4 > 65535) return TMFG_ETOOBIG;
+    const bool p1 = args.mode == TMFG_CORR && args.P == 1;
+    const size_t gen_smem = loop_smem_bytes(args.n, dtype, args.mode);
+    const bool corr1 = p1 && (shape.general == 0 || (shape.general < 0 && gen_smem > kSmemLimit));
     const bool heap = args.mode == TMFG_HEAP;
     auto kf = heap ? tmfg_loop_kernel<float, true> : tmfg_loop_kernel<float, false>;
     auto kd = heap ? tmfg_loop_kernel<double, true> : tmfg_loop_kernel<double, false>;
-    const void *kp = dtype == TMFG_F32 ? (const void *)kf : (const void *)kd;
-    if (cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(kp, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             carveout_percent(smem, 1)) != cudaSuccess)
-        return TMFG_ECUDA;
+    size_t smem;
+    bool gp = false;
+    if (corr1) {
+        if (!corr1_shape_ok(shape.threads, shape.lanes)) return TMFG_EINVAL;
+        int g = corr1_fit_groups(args.n, dtype, shape.groups, kSmemLimit, false);
+        if (g < 0) {
+            gp = true;
+            g = corr1_fit_groups(args.n, dtype, shape.groups, kSmemLimit, true);
+            if (g < 0) return TMFG_ETOOBIG;
+        }
+        smem = corr1_smem_bytes(args.n, dtype, g, gp);
+    } else {
+        smem = gen_smem;
+        if (smem > kSmemLimit) return TMFG_ETOOBIG;
+        const void *kp = dtype == TMFG_F32 ? (const void *)kf : (const void *)kd;
+        if (cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(kp, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 carveout_percent(smem, 1)) != cudaSuccess)
+            return TMFG_ECUDA;
+    }
     const int total = args.n - 4;
     int stops[8];
     int ns = 0;
@@ -1271,10 +1316,14 @@ int launch_loop(const LoopArgs &args, int dtype, cudaStream_t stream)
         LoopArgs a = args;
         a.k_stop = stops[i];
         a.resume = i > 0;
-        if (dtype == TMFG_F32)
+        if (corr1) {
+            const int rc = launch_corr1(a, shape, dtype, smem, gp, stream);
+            if (rc) return rc;
+        } else if (dtype == TMFG_F32) {
             kf<<<1, kLoopThreads, smem, stream>>>(a);
-        else
+        } else {
             kd<<<1, kLoopThreads, smem, stream>>>(a);
+        }
         if (i + 1 < ns)
             compact_rows_kernel<<<2 * sms, 256, 0, stream>>>(const_cast<uint16_t *>(args.idx),
                                                              args.ldi, args.n, args.state,
@@ -1283,11 +1332,22 @@ int launch_loop(const LoopArgs &args, int dtype, cudaStream_t stream)
     return cudaGetLastError() == cudaSuccess ? TMFG_OK : TMFG_ECUDA;
 }
 
-int launch_loop_batch(const LoopArgs *d_args, int count, int max_n, int dtype, int mode,
-                      cudaStream_t stream)
+int launch_loop_batch(const LoopArgs *d_args, int count, int max_n, int dtype, int mode, int P,
+                      cudaStream_t stream, const LoopShape &shape)
 {
+    if (2 * (size_t)max_n - 4 > 65535) return TMFG_ETOOBIG;
     const size_t smem = loop_smem_bytes(max_n, dtype, mode);
-    if (smem > kSmemLimit || 2 * (size_t)max_n - 4 > 65535) return TMFG_ETOOBIG;
+    if (mode == TMFG_CORR && P == 1 &&
+        (shape.general == 0 || (shape.general < 0 && smem > kSmemLimit))) {
+        if (!corr1_shape_ok(shape.threads, shape.lanes)) return TMFG_EINVAL;
+        // two CTAs per SM when they fit, else one
+        int g = corr1_fit_groups(max_n, dtype, shape.groups, kSmemLimit / 2 - 4096, false);
+        if (g < 0) g = corr1_fit_groups(max_n, dtype, shape.groups, kSmemLimit, false);
+        if (g < 0) return TMFG_ETOOBIG;
+        return launch_corr1_batch(d_args, count, shape, dtype,
+                                  corr1_smem_bytes(max_n, dtype, g, false), stream);
+    }
+    if (smem > kSmemLimit) return TMFG_ETOOBIG;
     const bool heap = mode == TMFG_HEAP;
     auto kf = heap ? tmfg_loop_batch_kernel<float, true> : tmfg_loop_batch_kernel<float, false>;
     auto kd = heap ? tmfg_loop_batch_kernel<double, true> : tmfg_loop_batch_kernel<double, false>;

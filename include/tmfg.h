@@ -302,6 +302,51 @@ enum { TMFG_SIM_F64 = 0, TMFG_SIM_F32 = 1, TMFG_SIM_BF16X3 = 2, TMFG_SIM_TF32X3 
 int tmfg_similarity(tmfg_ctx *ctx, const float *X, int64_t n, int64_t T, int32_t precision,
                     float *S, int64_t ld, void *stream);
 
+/* ------------------------------------------------------------ pipeline
+ * The whole clustering of many instances from their raw series (no
+ * counterpart in the paper: the request shape of a clustering service).
+ * For every job, in stream order: the Pearson similarity of its series into
+ * S (tmfg_similarity at `precision`); then the TMFG and exact APSP of all
+ * jobs through tmfg_batch_run (one launch per stage for all of them); then
+ * each job's DBHT dendrogram into Z (dbht_cluster) and, when k > 0, its cut
+ * at k clusters into labels (tmfg_cut_labels).  Every job gets exactly what
+ * those calls give it alone.  All pointers are caller-owned device memory. */
+typedef struct {
+    const float *X;         /* n x T series, row-major, row stride ldx >= T */
+    int64_t n, T, ldx;
+    float *S;               /* n x n similarity (written; ld = n) */
+    int32_t *order;         /* [n] */
+    int32_t *edges;         /* [(3n-6)*2] */
+    int32_t *ins_face;      /* [(n-4)*3] (may be NULL when n == 4) */
+    int32_t *bubble_parent; /* [n-3] */
+    float *D;               /* n x n exact APSP (written; ldd = n) */
+    double *Z;              /* (n-1) x 4 linkage, scipy layout (written) */
+    int32_t k;              /* clusters of the cut; 0 = no cut */
+    int32_t *labels;        /* [n] cluster of each series at k (k > 0) */
+} tmfg_pipeline_job;
+
+typedef struct {
+    int32_t precision;      /* TMFG_SIM_* of the similarity */
+    tmfg_params tmfg;       /* TMFG parameters (dtype must be TMFG_F32) */
+} tmfg_pipeline_params;
+
+/* Run the pipeline over `count` jobs (a HOST array of descriptors).
+ * TMFG_ETOOBIG if an n exceeds DBHT_MAX_N or tmfg_max_n_mode; data errors
+ * go to the status word (tmfg_sync_status).  Asynchronous. */
+int tmfg_pipeline_run(tmfg_ctx *ctx, const tmfg_pipeline_job *jobs, int32_t count,
+                      const tmfg_pipeline_params *params, const tmfg_batch_config *cfg,
+                      void *stream);
+
+/* Workspace one pipeline job of size n, length T needs in a lane. */
+size_t tmfg_pipeline_request_bytes(int64_t n, int64_t T, int32_t precision);
+
+/* Labels of the cut of a linkage Z ((n-1) x 4, device, scipy layout) at k
+ * clusters (Section 5: the clusters the ARI scores): the first n - k merges
+ * are applied; clusters are numbered 0..k-1 in the order of their smallest
+ * member.  labels: [n] device int32.  Asynchronous. */
+int tmfg_cut_labels(tmfg_ctx *ctx, const double *Z, int64_t n, int32_t k, int32_t *labels,
+                    void *stream);
+
 /* ------------------------------------------------------------ serving
  * A request server with continuous batching (no counterpart in the paper).
  * Jobs (tmfg_job, buffers resident in device memory, caller-owned) are
@@ -324,6 +369,9 @@ typedef struct {
     tmfg_params params;    /* TMFG parameters of every job */
     int32_t apsp;          /* 1: also the exact APSP into each job's D */
     int32_t sssp_threads;  /* as in tmfg_batch_config; 0 = default */
+    int32_t pipeline;      /* 1: jobs are whole pipelines (tmfg_serve_submit_pipeline,
+                              run by tmfg_pipeline_run; apsp is implied) */
+    int32_t precision;     /* TMFG_SIM_* of the pipelines' similarity */
 } tmfg_serve_config;
 
 typedef struct {
@@ -346,6 +394,12 @@ int tmfg_serve_start(tmfg_server **out, int device, const tmfg_serve_config *cfg
  * descriptor is copied; its buffers must stay valid until the job's result
  * has been polled. */
 int64_t tmfg_serve_submit(tmfg_server *s, const tmfg_job *job, void *stream);
+
+/* Queue one whole pipeline (a server started with pipeline = 1): the job
+ * runs through tmfg_pipeline_run with the other jobs of its batch, and gets
+ * exactly what that call gives it alone.  Admission counts
+ * tmfg_pipeline_request_bytes.  Returns its id or minus an error code. */
+int64_t tmfg_serve_submit_pipeline(tmfg_server *s, const tmfg_pipeline_job *job, void *stream);
 
 /* Move up to `max` finished jobs' results into out[] (waiting up to wait_us
  * microseconds for the first); returns the count, or minus an error code.

@@ -64,7 +64,20 @@ class _DbhtOutputs(ctypes.Structure):
 class _ServeConfig(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("lane_bytes", ctypes.c_size_t), ("params", _Params),
-                ("apsp", ctypes.c_int32), ("sssp_threads", ctypes.c_int32)]
+                ("apsp", ctypes.c_int32), ("sssp_threads", ctypes.c_int32),
+                ("pipeline", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+class _PipelineJob(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("n", ctypes.c_int64), ("T", ctypes.c_int64),
+                ("ldx", ctypes.c_int64), ("S", ctypes.c_void_p), ("order", ctypes.c_void_p),
+                ("edges", ctypes.c_void_p), ("ins_face", ctypes.c_void_p),
+                ("bubble_parent", ctypes.c_void_p), ("D", ctypes.c_void_p),
+                ("Z", ctypes.c_void_p), ("k", ctypes.c_int32), ("labels", ctypes.c_void_p)]
+
+
+class _PipelineParams(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("tmfg", _Params)]
 
 
 class _ServeResult(ctypes.Structure):
@@ -114,6 +127,16 @@ def load_library():
         lib.tmfg_batch_run.argtypes = [P, ctypes.POINTER(_Job), ctypes.c_int32,
                                        ctypes.POINTER(_Params), ctypes.POINTER(_BatchConfig), P]
         lib.tmfg_batch_run.restype = ctypes.c_int
+        lib.tmfg_pipeline_run.argtypes = [P, ctypes.POINTER(_PipelineJob), i32,
+                                          ctypes.POINTER(_PipelineParams),
+                                          ctypes.POINTER(_BatchConfig), P]
+        lib.tmfg_pipeline_run.restype = ctypes.c_int
+        lib.tmfg_pipeline_request_bytes.argtypes = [i64, i64, i32]
+        lib.tmfg_pipeline_request_bytes.restype = ctypes.c_size_t
+        lib.tmfg_cut_labels.argtypes = [P, P, i64, i32, P, P]
+        lib.tmfg_cut_labels.restype = ctypes.c_int
+        lib.tmfg_serve_submit_pipeline.argtypes = [P, ctypes.POINTER(_PipelineJob), P]
+        lib.tmfg_serve_submit_pipeline.restype = i64
         lib.tmfg_set_loop_shape.argtypes = [P, ctypes.POINTER(_LoopShape)]
         lib.tmfg_set_loop_shape.restype = ctypes.c_int
         lib.dbht_cluster.argtypes = [P, P, i64, i64, i32, P, P, P, P, P, i64, P, P]
@@ -465,6 +488,72 @@ def tmfg_batch_run(ctx: Context, mats, mode: str = "corr", prefix: int = 1, apsp
     return outs
 
 
+_SIM = {"f64": 0, "f32": 1, "bf16x3": 2, "tf32x3": 3}
+
+
+def _pipeline_outputs(n, dev):
+    torch = _torch()
+    return {"S": torch.empty((n, n), dtype=torch.float32, device=dev),
+            "order": torch.empty(n, dtype=torch.int32, device=dev),
+            "edges": torch.empty((3 * n - 6, 2), dtype=torch.int32, device=dev),
+            "ins_face": torch.empty((max(n - 4, 1), 3), dtype=torch.int32, device=dev),
+            "bubble_parent": torch.empty(n - 3, dtype=torch.int32, device=dev),
+            "D": torch.empty((n, n), dtype=torch.float32, device=dev),
+            "Z": torch.empty((n - 1, 4), dtype=torch.float64, device=dev),
+            "labels": torch.empty(n, dtype=torch.int32, device=dev)}
+
+
+def _pipeline_job(X, k, o):
+    torch = _torch()
+    if X.dtype != torch.float32 or X.dim() != 2 or X.stride(1) != 1:
+        raise TypeError("X must be a row-major float32 matrix (series x length)")
+    n, T = X.shape
+    return _PipelineJob(X.data_ptr(), n, T, X.stride(0), o["S"].data_ptr(), o["order"].data_ptr(),
+                        o["edges"].data_ptr(), o["ins_face"].data_ptr(),
+                        o["bubble_parent"].data_ptr(), o["D"].data_ptr(), o["Z"].data_ptr(),
+                        int(k), o["labels"].data_ptr() if k > 0 else None)
+
+
+def tmfg_pipeline_run(ctx: Context, series, ks, precision: str = "bf16x3", mode: str = "corr",
+                      prefix: int = 1, outs=None, stream=None, sssp_threads: int = 0,
+                      loop_shape=None):
+    """The whole clustering of every instance: similarity of its series (a
+    float32 CUDA tensor, series x length), TMFG and exact APSP (batched), DBHT
+    linkage and the labels of its cut at k (ks[i]; 0 = no cut).  Returns a
+    list of dicts with S, the TMFG arrays, D, Z and labels.  Asynchronous."""
+    if not series:
+        return []
+    if outs is None:
+        outs = [_pipeline_outputs(X.shape[0], X.device) for X in series]
+    jobs = (_PipelineJob * len(series))()
+    for i, (X, k, o) in enumerate(zip(series, ks, outs)):
+        jobs[i] = _pipeline_job(X, k, o)
+    pp = _PipelineParams(_SIM[precision],
+                         _Params({"corr": TMFG_CORR, "heap": TMFG_HEAP}[mode], int(prefix),
+                                 TMFG_F32, 0))
+    cfg = _BatchConfig(int(sssp_threads), _loop_shape(loop_shape))
+    _check(load_library().tmfg_pipeline_run(ctx.handle, jobs, len(series), ctypes.byref(pp),
+                                            ctypes.byref(cfg), _stream_handle(stream)),
+           "tmfg_pipeline_run")
+    return outs
+
+
+def tmfg_pipeline_request_bytes(n: int, T: int, precision: str = "bf16x3") -> int:
+    return int(load_library().tmfg_pipeline_request_bytes(int(n), int(T), _SIM[precision]))
+
+
+def tmfg_cut_labels(ctx: Context, Z, k: int, labels=None, stream=None):
+    """Labels (int32 CUDA tensor) of the cut of linkage Z at k clusters."""
+    torch = _torch()
+    n = Z.shape[0] + 1
+    if labels is None:
+        labels = torch.empty(n, dtype=torch.int32, device=Z.device)
+    _check(load_library().tmfg_cut_labels(ctx.handle, _dev_ptr(Z, torch.float64), n, int(k),
+                                          _dev_ptr(labels, torch.int32), _stream_handle(stream)),
+           "tmfg_cut_labels")
+    return labels
+
+
 class Server:
     """Owns a tmfg_server (continuous-batching request server) and keeps each
     request's tensors alive until its result has been polled."""
@@ -496,13 +585,31 @@ class Server:
 
 def tmfg_serve_start(device: int = 0, lanes: int = 0, max_batch: int = 0, lane_bytes: int = 0,
                      mode: str = "corr", prefix: int = 1, dtype: int = TMFG_F32,
-                     apsp: bool = True, sssp_threads: int = 0) -> Server:
-    """Start a request server (see tmfg_serve_start in include/tmfg.h)."""
+                     apsp: bool = True, sssp_threads: int = 0, pipeline: bool = False,
+                     precision: str = "bf16x3") -> Server:
+    """Start a request server (see tmfg_serve_start in include/tmfg.h); with
+    ``pipeline`` its jobs are whole clusterings from raw series
+    (tmfg_serve_submit_pipeline)."""
     cfg = _ServeConfig(int(lanes), int(max_batch), int(lane_bytes),
                        _Params({"corr": TMFG_CORR, "heap": TMFG_HEAP}[mode], int(prefix),
                                int(dtype), 0),
-                       1 if apsp else 0, int(sssp_threads))
+                       1 if apsp else 0, int(sssp_threads), 1 if pipeline else 0,
+                       _SIM[precision])
     return Server(device, cfg)
+
+
+def tmfg_serve_submit_pipeline(server: Server, X, k: int, out=None, stream=None) -> int:
+    """Queue the whole clustering of series X (float32 CUDA, series x length)
+    with its cut at k; returns the request id.  Outputs as tmfg_pipeline_run's."""
+    if out is None:
+        out = _pipeline_outputs(X.shape[0], X.device)
+    job = _pipeline_job(X, k, out)
+    rid = load_library().tmfg_serve_submit_pipeline(server.handle, ctypes.byref(job),
+                                                    _stream_handle(stream))
+    if rid < 0:
+        raise TmfgError(int(-rid), "tmfg_serve_submit_pipeline")
+    server.live[int(rid)] = (X, out)
+    return int(rid)
 
 
 def tmfg_serve_submit(server: Server, S, out=None, stream=None) -> int:

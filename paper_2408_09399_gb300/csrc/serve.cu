@@ -35,6 +35,7 @@ int64_t now_ns()
 struct Request {
     int64_t id;
     tmfg_job job;
+    tmfg_pipeline_job pjob;  // pipeline servers
     size_t bytes;
     int64_t t_submit;
     cudaEvent_t ready;  // recorded on the submitter's stream
@@ -113,8 +114,16 @@ void launch(tmfg_server *s, Lane &l)
     }
     tmfg_batch_config bc{};
     bc.sssp_threads = s->cfg.sssp_threads;
-    if (rc == TMFG_OK)
+    if (rc == TMFG_OK && s->cfg.pipeline) {
+        std::vector<tmfg_pipeline_job> pj(l.reqs.size());
+        for (size_t i = 0; i < l.reqs.size(); ++i) pj[i] = l.reqs[i].pjob;
+        tmfg_pipeline_params pp{};
+        pp.precision = s->cfg.precision;
+        pp.tmfg = s->params;
+        rc = tmfg_pipeline_run(l.ctx, pj.data(), (int)pj.size(), &pp, &bc, l.stream);
+    } else if (rc == TMFG_OK) {
         rc = tmfg_batch_run(l.ctx, jobs.data(), (int)jobs.size(), &s->params, &bc, l.stream);
+    }
     l.launch_rc = rc;
     *l.h_status = 0;
     cudaMemcpyAsync(l.h_status, l.ctx->status, sizeof(int), cudaMemcpyDeviceToHost, l.stream);
@@ -184,6 +193,37 @@ void worker_main(tmfg_server *s)
     }
 }
 
+// Admit request r (bytes set) to the queue once the submitter's stream
+// reaches this point; returns its id or minus an error code.
+int64_t enqueue(tmfg_server *s, Request &r, void *stream)
+{
+    if (r.bytes + batch_table_bytes(1, s->cfg.apsp ? 1 : 0) > s->cfg.lane_bytes)
+        return -TMFG_ENOMEM;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        if (s->stop) return -TMFG_EINVAL;
+        if (!s->event_pool.empty()) {
+            r.ready = s->event_pool.back();
+            s->event_pool.pop_back();
+        }
+    }
+    DeviceGuard g(s->device);
+    if (!g.ok) return -TMFG_ECUDA;
+    if (!r.ready && cudaEventCreateWithFlags(&r.ready, cudaEventDisableTiming) != cudaSuccess)
+        return -TMFG_ECUDA;
+    // the job's inputs are ready once the submitter's stream reaches here
+    if (cudaEventRecord(r.ready, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+        cudaEventDestroy(r.ready);
+        return -TMFG_ECUDA;
+    }
+    std::lock_guard<std::mutex> lg(s->mu);
+    r.id = s->next_id++;
+    r.t_submit = now_ns();
+    s->queue.push_back(r);
+    s->cv.notify_all();
+    return r.id;
+}
+
 void free_lanes(tmfg_server *s)
 {
     DeviceGuard g(s->device);
@@ -244,6 +284,9 @@ int tmfg_serve_start(tmfg_server **out, int device, const tmfg_serve_config *cfg
         return TMFG_EINVAL;
     if (cfg->sssp_threads && cfg->sssp_threads != 256 && cfg->sssp_threads != 512)
         return TMFG_EINVAL;
+    if (cfg->pipeline && (p.dtype != TMFG_F32 || cfg->precision < TMFG_SIM_F64 ||
+                          cfg->precision > TMFG_SIM_TF32X3))
+        return TMFG_EINVAL;
     tmfg_server *s = new (std::nothrow) tmfg_server();
     if (!s) return TMFG_ENOMEM;
     s->device = device;
@@ -252,6 +295,7 @@ int tmfg_serve_start(tmfg_server **out, int device, const tmfg_serve_config *cfg
     if (!s->cfg.max_batch) s->cfg.max_batch = 256;
     if (!s->cfg.lane_bytes) s->cfg.lane_bytes = (size_t)4 << 30;
     s->params = p;
+    if (s->cfg.pipeline) s->cfg.apsp = 1;  // the dendrogram needs the distances
     s->lanes.resize(s->cfg.lanes);
     int rc = TMFG_OK;
     {
@@ -299,31 +343,25 @@ int64_t tmfg_serve_submit(tmfg_server *s, const tmfg_job *job, void *stream)
     r.job = J;
     if (!s->cfg.apsp) r.job.D = nullptr;
     r.bytes = batch_request_bytes(J.n, s->cfg.apsp != 0);
-    if (r.bytes + batch_table_bytes(1, s->cfg.apsp ? 1 : 0) > s->cfg.lane_bytes)
-        return -TMFG_ENOMEM;
-    {
-        std::lock_guard<std::mutex> g(s->mu);
-        if (s->stop) return -TMFG_EINVAL;
-        if (!s->event_pool.empty()) {
-            r.ready = s->event_pool.back();
-            s->event_pool.pop_back();
-        }
-    }
-    DeviceGuard g(s->device);
-    if (!g.ok) return -TMFG_ECUDA;
-    if (!r.ready && cudaEventCreateWithFlags(&r.ready, cudaEventDisableTiming) != cudaSuccess)
-        return -TMFG_ECUDA;
-    // the job's inputs are ready once the submitter's stream reaches here
-    if (cudaEventRecord(r.ready, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
-        cudaEventDestroy(r.ready);
-        return -TMFG_ECUDA;
-    }
-    std::lock_guard<std::mutex> lg(s->mu);
-    r.id = s->next_id++;
-    r.t_submit = now_ns();
-    s->queue.push_back(r);
-    s->cv.notify_all();
-    return r.id;
+    return enqueue(s, r, stream);
+}
+
+int64_t tmfg_serve_submit_pipeline(tmfg_server *s, const tmfg_pipeline_job *job, void *stream)
+{
+    if (!s || !job || !s->cfg.pipeline) return -TMFG_EINVAL;
+    const tmfg_pipeline_job &J = *job;
+    if (!J.X || !J.S || !J.order || !J.edges || !J.bubble_parent || !J.D || !J.Z || J.n < 4 ||
+        J.T < 2 || J.ldx < J.T || (J.n > 4 && !J.ins_face) || J.k < 0 || J.k > J.n ||
+        (J.k > 0 && !J.labels))
+        return -TMFG_EINVAL;
+    if (J.n > tmfg_max_n_mode(s->params.dtype, s->params.mode, s->params.prefix) ||
+        J.n > DBHT_MAX_N)
+        return -TMFG_ETOOBIG;
+    Request r{};
+    r.pjob = J;
+    r.job.n = J.n;
+    r.bytes = tmfg_pipeline_request_bytes(J.n, J.T, s->cfg.precision);
+    return enqueue(s, r, stream);
 }
 
 int tmfg_serve_poll(tmfg_server *s, tmfg_serve_result *out, int32_t max, int32_t wait_us)

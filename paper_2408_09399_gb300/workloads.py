@@ -221,7 +221,8 @@ def random_similarity(seed: int, n: int, dtype=np.float32, kind: str = "uniform"
 
 
 def serving_requests(seed: int, count: int, device: str = "cuda", n_range=(64, 4000),
-                     T_range=(128, 2048), k_range=(2, 30), loading=(0.5, 0.9)):
+                     T_range=(128, 2048), k_range=(2, 30), loading=(0.5, 0.9),
+                     similarity: bool = True):
     """Clustering requests shaped like the serving workload: n log-uniform in
     n_range, series length T uniform in T_range, planted cluster count k
     uniform in k_range, strong loadings (clean instances).  The sizes come
@@ -229,7 +230,9 @@ def serving_requests(seed: int, count: int, device: str = "cuda", n_range=(64, 4
     with torch's generator seeded from (seed, request), on ``device``, which
     keeps generation of thousands of requests fast (they are reproducible on
     one device type, not across CPU and GPU).  Returns a list of dicts with
-    the float32 Pearson matrix S, the labels and the shape."""
+    the raw float32 series X (n x T), the float32 Pearson matrix S (unless
+    ``similarity`` is False: the pipeline computes it), the labels and the
+    shape."""
     import torch
     u = uniform(seed, "req_n", count)
     ns = np.round(np.exp(np.log(n_range[0]) + u * (np.log(n_range[1]) - np.log(n_range[0]))))
@@ -244,9 +247,12 @@ def serving_requests(seed: int, count: int, device: str = "cuda", n_range=(64, 4
         lam = loading[0] + (loading[1] - loading[0]) * torch.rand(n, generator=g, device=device)
         F = torch.randn(k, T, generator=g, device=device)
         X = lam[:, None] * F[lab] + torch.randn(n, T, generator=g, device=device)
-        X = X - X.mean(dim=1, keepdim=True)
-        X = X / torch.sqrt((X * X).sum(dim=1, keepdim=True))
-        S = X @ X.T
-        S.fill_diagonal_(1.0)
-        out.append({"S": S.contiguous(), "labels": lab, "n": n, "T": T, "k": k})
+        rec = {"X": X.contiguous(), "labels": lab, "n": n, "T": T, "k": k}
+        if similarity:
+            Y = X - X.mean(dim=1, keepdim=True)
+            Y = Y / torch.sqrt((Y * Y).sum(dim=1, keepdim=True))
+            S = Y @ Y.T
+            S.fill_diagonal_(1.0)
+            rec["S"] = S.contiguous()
+        out.append(rec)
     return out

@@ -86,9 +86,9 @@ def parse():
     ap.add_argument("--n", type=int, default=20000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batch-requests", type=int, default=512)
+    ap.add_argument("--batch-requests", type=int, default=4096)
     ap.add_argument("--no-batch", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=2048)
+    ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-sim", action="store_true")
     ap.add_argument("--sim-only", action="store_true",
@@ -266,6 +266,7 @@ def run_similarity(T, ctx, stream, n_series=None):
         e = t["edges"].cpu().numpy()
         return {(int(min(a, b)), int(max(a, b))) for a, b in e}
 
+    T.tmfg_set_loop_shape(ctx, None)  # the automatic kernel choice holds every n
     e_ref = edges_of(ref)
     for prec in ("bf16x3", "tf32x3", "f32"):
         d = (out[prec] - ref).abs_()
@@ -307,6 +308,9 @@ def run_ours(args, rank, world, local):
     Da = torch.empty((n, n), dtype=torch.float32, device=dev)
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    # the loop's launch shape for this n, chosen by timing every candidate
+    from paper_2408_09399_gb300 import autotune
+    loop_tune = autotune.tune_loop(ctx, S, MODE, 1)
 
     def step(times=None):
         e0, e1, e2, e3 = ev(), ev(), ev(), ev()
@@ -464,17 +468,35 @@ def run_ours(args, rank, world, local):
         T.tmfg_sync_status(ctx, stream)
         same = (torch.equal(host["edges"], edges_step.cpu()) and torch.equal(host["D"], D.cpu())
                 and torch.equal(host["D_approx"], Da.cpu()))
-        a, b = ev(), ev()
-        k = max(1, min(args.steps, 3))
-        a.record(stream)
+        # every step timed on its own, its stages read back after it
+        k = max(1, args.steps)
+        per, stages = [], []
         for _ in range(k):
+            a, b = ev(), ev()
+            a.record(stream)
             e2e_step()
-        b.record(stream)
-        T.tmfg_sync_status(ctx, stream)
+            b.record(stream)
+            T.tmfg_sync_status(ctx, stream)
+            per.append(a.elapsed_time(b))
+            stages.append(T.tmfg_solve_host_stages(ctx))
         out_bytes = sum(v.numel() * v.element_size() for v in host.values())
-        e2e = {"value": round(a.elapsed_time(b) / k, 3), "unit": "ms",
+        med = int(np.argsort(per)[len(per) // 2])
+        # the link itself: one plain copy of the page-locked S to the device
+        dst = torch.empty_like(Sh, device=dev)
+        a, b = ev(), ev()
+        a.record(stream)
+        dst.copy_(Sh, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        h2d_gbs = Sh.numel() * 4 / (a.elapsed_time(b) * 1e-3) / 1e9
+        del dst
+        e2e = {"value": round(float(np.mean(per)), 3), "unit": "ms",
                "h2d_bytes_per_step": 4 * n * n, "d2h_bytes_per_step": int(out_bytes),
                "api": "tmfg_solve_host (host buffers, page-locked)",
+               "steps": k, "per_step_ms": [round(x, 3) for x in per],
+               "stages_ms_median_step": stages[med],
+               "device_step_ms": round(ms_step, 3),
+               "h2d_plain_copy_gbs": round(h2d_gbs, 1),
                "outputs_equal_device_path": bool(same)}
 
     result = {
@@ -493,6 +515,7 @@ def run_ours(args, rank, world, local):
             "warp_refreshes": stats["cycles_validate"],
             "warp_refresh_steps": stats["cycles_resolve"]},
         "tmfg_variants": alt,
+        "loop_autotune": loop_tune,
         "dbht": dbht,
         "roofline": roofline,
         "algorithmic_bytes_per_step": int(14 * n * n),
@@ -501,90 +524,147 @@ def run_ours(args, rank, world, local):
         "e2e": e2e,
         "gpu_launches": kernels_per_step(n) * args.steps,
     }
+    section_s = {}
+
+    def section(name, fn):
+        t0 = time.time()
+        result[name] = fn()
+        section_s[name] = round(time.time() - t0, 1)
+        print(f"[bench] {name} done in {section_s[name]} s", file=sys.stderr, flush=True)
+
+    Sn = S.cpu().numpy() if rank == 0 and world == 1 and not args.no_cpu_baseline else None
+    del S, D, Da
+    torch.cuda.empty_cache()
+    shared = {}
     if not args.no_batch:
-        result["batched"] = run_batched(T, ctx, args.batch_requests, stream)
+        section("batched", lambda: run_batched(T, ctx, args.batch_requests, stream, shared))
     if not args.no_serve:
-        result["serving"] = run_serving(T, ctx, args.serve_requests, stream)
+        section("serving", lambda: run_serving(T, ctx, args.serve_requests, stream,
+                                               shared=shared))
+    shared.clear()
     if not args.no_sim:
-        result["similarity"] = run_similarity(T, ctx, stream, args.sim_n)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(S.cpu().numpy(), n)
+        section("similarity", lambda: run_similarity(T, ctx, stream, args.sim_n))
+    if Sn is not None:
+        section("cpu_baseline", lambda: cpu_baseline(Sn, n))
+    result["section_s"] = section_s
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return result
 
 
-def run_batched(T, ctx, nreq, stream):
-    """Many small clustering instances (the serving request shape: n
-    log-uniform in [64, 4000], T in [128, 2048], 2-30 planted clusters):
-    TMFG (corr-tmfg P=1) + exact APSP per request, one instance per launch
-    sequence versus tmfg_batch_run, plain and replayed from a CUDA graph."""
+PIPE_PRECISION = "bf16x3"
+
+
+def pipeline_requests(seed, nreq):
+    """The serving workload: nreq clustering requests from raw series (n
+    log-uniform in [64, 4000], T uniform in [128, 2048], 2-30 planted
+    clusters, k = the planted count)."""
+    import torch
+    from paper_2408_09399_gb300 import workloads as W
+    return W.serving_requests(seed, nreq, device=f"cuda:{torch.cuda.current_device()}",
+                              similarity=False)
+
+
+class PlainPath:
+    """One request at a time through the single calls (similarity, TMFG,
+    exact APSP, DBHT, cut), with the n x n buffers reused across requests;
+    the small outputs (edges, linkage, labels) of each request are kept."""
+
+    def __init__(self, T, ctx, nmax, stream):
+        import torch
+        self.T, self.ctx, self.stream = T, ctx, stream
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.S = torch.empty(nmax * nmax, dtype=torch.float32, device=dev)
+        self.D = torch.empty(nmax * nmax, dtype=torch.float32, device=dev)
+
+    def run(self, X, k, keep=None):
+        import torch
+        T, ctx, st = self.T, self.ctx, self.stream
+        n = X.shape[0]
+        dev = X.device
+        S = self.S[: n * n].view(n, n)
+        D = self.D[: n * n].view(n, n)
+        o = keep if keep is not None else {
+            "order": torch.empty(n, dtype=torch.int32, device=dev),
+            "edges": torch.empty((3 * n - 6, 2), dtype=torch.int32, device=dev),
+            "ins_face": torch.empty((max(n - 4, 1), 3), dtype=torch.int32, device=dev),
+            "bubble_parent": torch.empty(n - 3, dtype=torch.int32, device=dev),
+            "Z": torch.empty((n - 1, 4), dtype=torch.float64, device=dev),
+            "labels": torch.empty(n, dtype=torch.int32, device=dev)}
+        T.tmfg_similarity(ctx, X, PIPE_PRECISION, S=S, stream=st)
+        T.tmfg_build(ctx, S, MODE, 1, out=o, stream=st)
+        T.tmfg_apsp(ctx, S, o["edges"], D=D, stream=st)
+        T.dbht_cluster(ctx, S, o, D, linkage=o["Z"], stream=st)
+        T.tmfg_cut_labels(ctx, o["Z"], k, labels=o["labels"], stream=st)
+        return o
+
+
+def same_results(a, b):
+    import torch
+    return all(torch.equal(a[key], b[key]) for key in ("edges", "Z", "labels"))
+
+
+def run_batched(T, ctx, nreq, stream, shared=None):
+    """The serving workload as one batch: every request's whole clustering
+    (similarity from its raw series, TMFG corr P=1, exact APSP, DBHT, labels
+    at its k) through tmfg_pipeline_run, chunked as the autotuner chose,
+    plain and replayed from CUDA graphs, against the plain path (one request
+    at a time through the single calls)."""
     import torch
     from paper_2408_09399_gb300 import autotune
-    from paper_2408_09399_gb300 import workloads as W
-    reqs = W.serving_requests(1005, nreq, device=f"cuda:{torch.cuda.current_device()}")
-    mats = [r["S"] for r in reqs]
-    dev = mats[0].device
-
-    def alloc():
-        outs = []
-        for S in mats:
-            n = S.shape[0]
-            outs.append({"order": torch.empty(n, dtype=torch.int32, device=dev),
-                         "edges": torch.empty((3 * n - 6, 2), dtype=torch.int32, device=dev),
-                         "ins_face": torch.empty((n - 4, 3), dtype=torch.int32, device=dev),
-                         "bubble_parent": torch.empty(n - 3, dtype=torch.int32, device=dev),
-                         "D": torch.empty((n, n), dtype=torch.float32, device=dev)})
-        return outs
-
+    reqs = pipeline_requests(1005, nreq)
+    Xs = [r["X"] for r in reqs]
+    ks = [r["k"] for r in reqs]
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-    # plain: one instance per launch sequence, in arrival order
-    plain = alloc()
-    for S, o in zip(mats[:4], plain[:4]):
-        T.tmfg_build(ctx, S, MODE, 1, out=o, stream=stream)
-        T.tmfg_apsp(ctx, S, o["edges"], D=o["D"], stream=stream)
+    nmax = max(r["n"] for r in reqs)
+    if shared is not None:
+        shared["reqs"] = reqs
+    plain = PlainPath(T, ctx, nmax, stream)
+    for X, k in zip(Xs[:4], ks[:4]):
+        plain.run(X, k)
     T.tmfg_sync_status(ctx, stream)
     marks = [ev() for _ in range(nreq + 1)]
     marks[0].record(stream)
-    for i, (S, o) in enumerate(zip(mats, plain)):
-        T.tmfg_build(ctx, S, MODE, 1, out=o, stream=stream)
-        T.tmfg_apsp(ctx, S, o["edges"], D=o["D"], stream=stream)
+    plain_out = []
+    for i, (X, k) in enumerate(zip(Xs, ks)):
+        plain_out.append(plain.run(X, k))
         marks[i + 1].record(stream)
     T.tmfg_sync_status(ctx, stream)
     lat = [marks[i].elapsed_time(marks[i + 1]) for i in range(nreq)]
     plain_ms = marks[0].elapsed_time(marks[-1])
-    # batched, launch shapes from the autotuner
-    cfg = autotune.tune_batch(ctx, mats[: min(nreq, 128)], MODE, 1, repeats=2)
-    batched = alloc()
+    if shared is not None:
+        shared["service_ms"] = lat
+    del plain
+    # batched, shapes from the autotuner (tuned on a sample of the requests)
+    cfg = autotune.tune_pipeline(ctx, Xs[: min(nreq, 256)], ks[: min(nreq, 256)],
+                                 PIPE_PRECISION, repeats=2)
     chunk = cfg["chunk"]
+    outs = [T._pipeline_outputs(X.shape[0], X.device) for X in Xs]
 
-    def run_all():
+    def run_all(st):
         for i in range(0, nreq, chunk):
-            T.tmfg_batch_run(ctx, mats[i:i + chunk], MODE, 1, apsp=True,
-                             sssp_threads=cfg["sssp_threads"], outs=batched[i:i + chunk],
-                             stream=stream)
+            T.tmfg_pipeline_run(ctx, Xs[i:i + chunk], ks[i:i + chunk], PIPE_PRECISION,
+                                outs=outs[i:i + chunk], stream=st,
+                                sssp_threads=cfg["sssp_threads"], loop_shape=cfg["loop"])
 
-    run_all()
+    run_all(stream)
     T.tmfg_sync_status(ctx, stream)
     a, b = ev(), ev()
     a.record(stream)
-    run_all()
+    run_all(stream)
     b.record(stream)
     T.tmfg_sync_status(ctx, stream)
     batch_ms = a.elapsed_time(b)
-    same = all(torch.equal(x["edges"], y["edges"]) and torch.equal(x["D"], y["D"])
-               for x, y in zip(plain, batched))
-    # the batched run replayed from a captured CUDA graph (one launch per
-    # chunk, so the graph needs a single chunk to replay unchanged)
+    same = all(same_results(x, y) for x, y in zip(plain_out, outs))
+    # the same launches captured once into a CUDA graph and replayed
     graph_ms = None
-    if chunk >= nreq:
+    try:
         g = torch.cuda.CUDAGraph()
         cs = torch.cuda.Stream()
         cs.wait_stream(stream)
         with torch.cuda.graph(g, stream=cs):
-            T.tmfg_batch_run(ctx, mats, MODE, 1, apsp=True, sssp_threads=cfg["sssp_threads"],
-                             outs=batched, stream=cs)
+            run_all(cs)
         stream.wait_stream(cs)
         g.replay()
         T.tmfg_sync_status(ctx, stream)
@@ -594,17 +674,47 @@ def run_batched(T, ctx, nreq, stream):
         b.record(stream)
         T.tmfg_sync_status(ctx, stream)
         graph_ms = a.elapsed_time(b)
-        same = same and all(torch.equal(x["edges"], y["edges"]) for x, y in zip(plain, batched))
-    lat_sorted = sorted(lat)
-    ns = [int(S.shape[0]) for S in mats]
+        same = same and all(same_results(x, y) for x, y in zip(plain_out, outs))
+        del g
+    except Exception as e:  # report, do not hide, a capture failure
+        graph_ms = f"capture failed: {type(e).__name__}: {e}"[:200]
+    # the TMFG + exact APSP stages alone, batched over the same similarity
+    # matrices (the stage the batched launch replaces one-instance launches in)
+    mats = [o["S"] for o in outs]
+    cfg_b = autotune.tune_batch(ctx, mats[: min(nreq, 256)], MODE, 1, repeats=2)
+    tdo = [{k2: o[k2] for k2 in ("order", "edges", "ins_face", "bubble_parent", "D")}
+           for o in outs]
+
+    def run_tmfg(st):
+        ch = cfg_b["chunk"]
+        for i in range(0, nreq, ch):
+            T.tmfg_batch_run(ctx, mats[i:i + ch], MODE, 1, apsp=True,
+                             sssp_threads=cfg_b["sssp_threads"], outs=tdo[i:i + ch], stream=st,
+                             loop_shape=cfg_b["loop"])
+
+    run_tmfg(stream)
+    T.tmfg_sync_status(ctx, stream)
+    a, b = ev(), ev()
+    a.record(stream)
+    run_tmfg(stream)
+    b.record(stream)
+    T.tmfg_sync_status(ctx, stream)
+    tmfg_ms = a.elapsed_time(b)
+    same = same and all(torch.equal(x["edges"], o["edges"]) for x, o in zip(plain_out, outs))
+    ns = [r["n"] for r in reqs]
+    del outs, plain_out, mats, tdo
+    torch.cuda.empty_cache()
     return {"requests": nreq, "n_range": [min(ns), max(ns)], "n_mean": round(float(np.mean(ns)), 1),
-            "tmfg": "corr-tmfg P=1 + exact APSP",
+            "pipeline": f"similarity ({PIPE_PRECISION}) -> corr-tmfg P=1 -> exact APSP -> DBHT "
+                        "-> labels at k",
+            "batched_tmfg_apsp_solves_per_s": round(nreq / (tmfg_ms / 1e3), 1),
+            "batched_tmfg_apsp_autotune": cfg_b,
             "plain_solves_per_s": round(nreq / (plain_ms / 1e3), 1),
-            "plain_p50_ms": round(lat_sorted[len(lat) // 2], 3),
-            "plain_p99_ms": round(lat_sorted[min(len(lat) - 1, int(0.99 * len(lat)))], 3),
+            "plain_p50_ms": round(pct(lat, 0.5), 3), "plain_p99_ms": round(pct(lat, 0.99), 3),
             "batched_solves_per_s": round(nreq / (batch_ms / 1e3), 1),
             "batched_ms": round(batch_ms, 3),
-            "graph_solves_per_s": round(nreq / (graph_ms / 1e3), 1) if graph_ms else None,
+            "graph_solves_per_s": (round(nreq / (graph_ms / 1e3), 1)
+                                   if isinstance(graph_ms, float) else graph_ms),
             "speedup_vs_plain": round(plain_ms / batch_ms, 2),
             "autotune": cfg, "outputs_identical": bool(same)}
 
@@ -622,51 +732,58 @@ def pct(xs, q):
     return xs[min(len(xs) - 1, int(q * len(xs)))]
 
 
-def run_serving(T, ctx, nreq, stream, lanes=3):
-    """Served clustering requests (TMFG corr P=1 + exact APSP each; n
-    log-uniform in [64, 4000], T in [128, 2048], 2-30 planted clusters)
-    arriving by a Poisson process at 0.8x and 1.5x the plain path's measured
-    capacity, through the continuous-batching server and through the plain
-    one-instance path under the same arrival times; then every request at
-    once.  Latency = completion seen by the host - arrival."""
+def fifo_replay(arr_s, service_ms):
+    """Latencies (ms) of a single FIFO server given arrival times (s) and each
+    request's service time (ms): what the plain one-request-at-a-time path
+    gives under that arrival process (its queue is exactly this)."""
+    t, lat = 0.0, []
+    for a, sv in zip(arr_s, service_ms):
+        start = max(t, a * 1e3)
+        t = start + sv
+        lat.append(t - a * 1e3)
+    return lat
+
+
+def run_serving(T, ctx, nreq, stream, lanes=3, shared=None):
+    """Served clustering requests, each the whole pipeline from raw series
+    (as in run_batched), arriving by a Poisson process at 0.8x and 1.5x the
+    plain path's measured capacity, through the continuous-batching server;
+    the plain path measured under the 0.8x arrivals, and at 1.5x (where it
+    saturates) its FIFO queue replayed from its measured per-request service
+    times; then every request at once.  Latency = completion seen by the host
+    - arrival."""
     import torch
-    from paper_2408_09399_gb300 import workloads as W
-    dev = torch.device("cuda", torch.cuda.current_device())
-    reqs = W.serving_requests(2005, nreq, device=str(dev))
-    mats = [r["S"] for r in reqs]
+    # the requests (and the plain path's service times) of the batched
+    # section when it ran, else generated here
+    if shared and len(shared.get("reqs", [])) == nreq:
+        reqs = shared["reqs"]
+    else:
+        reqs = pipeline_requests(1005, nreq)
+    Xs = [r["X"] for r in reqs]
+    ks = [r["k"] for r in reqs]
     torch.cuda.synchronize()
-
-    def outputs(S):
-        n = S.shape[0]
-        return {"order": torch.empty(n, dtype=torch.int32, device=dev),
-                "edges": torch.empty((3 * n - 6, 2), dtype=torch.int32, device=dev),
-                "ins_face": torch.empty((n - 4, 3), dtype=torch.int32, device=dev),
-                "bubble_parent": torch.empty(n - 3, dtype=torch.int32, device=dev),
-                "D": torch.empty((n, n), dtype=torch.float32, device=dev)}
-
-    served_out = [outputs(S) for S in mats]
-    nmax = max(int(S.shape[0]) for S in mats)
-    scratch = outputs(torch.empty((nmax, nmax), device=dev))
+    nmax = max(r["n"] for r in reqs)
+    plain = PlainPath(T, ctx, nmax, stream)
     now = T.tmfg_serve_now_ns
+    served_out = [T._pipeline_outputs(X.shape[0], X.device) for X in Xs]
 
-    def plain_one(S, o):
-        n = S.shape[0]
-        oo = o if o is not None else {
-            "order": scratch["order"][:n], "edges": scratch["edges"][: 3 * n - 6],
-            "ins_face": scratch["ins_face"][: n - 4], "bubble_parent": scratch["bubble_parent"][: n - 3]}
-        D = o["D"] if o is not None else scratch["D"].view(-1)[: n * n].view(n, n)
-        T.tmfg_build(ctx, S, MODE, 1, out=oo, stream=stream)
-        T.tmfg_apsp(ctx, S, oo["edges"], D=D, stream=stream)
+    def plain_one(i, keep=None):
+        o = plain.run(Xs[i], ks[i], keep)
         T.tmfg_sync_status(ctx, stream)
+        return o
 
-    # plain capacity on the first requests (service time alone, no queueing)
-    k_cap = min(nreq, 256)
-    for S in mats[:4]:
-        plain_one(S, None)
-    t0 = now()
-    for S in mats[:k_cap]:
-        plain_one(S, None)
-    cap = k_cap / ((now() - t0) / 1e9)
+    # plain service times (no queueing) of every request, measured
+    if shared and len(shared.get("service_ms", [])) == nreq:
+        service = shared["service_ms"]
+    else:
+        for i in range(4):
+            plain_one(i)
+        service = []
+        for i in range(nreq):
+            t0 = now()
+            plain_one(i)
+            service.append((now() - t0) / 1e6)
+    cap = 1e3 / float(np.mean(service))
 
     def wait_until(t_ns):
         while True:
@@ -679,21 +796,22 @@ def run_serving(T, ctx, nreq, stream, lanes=3):
     def run_plain(arr_s):
         base = now() + 2_000_000
         lat = []
-        for i, S in enumerate(mats):
+        for i in range(nreq):
             t_arr = base + int(arr_s[i] * 1e9)
             wait_until(t_arr)
-            plain_one(S, None)
+            plain_one(i)
             lat.append((now() - t_arr) / 1e6)
         span = (now() - base) / 1e9
         return {"solves_per_s": round(nreq / span, 1), "p50_ms": round(pct(lat, 0.5), 3),
-                "p99_ms": round(pct(lat, 0.99), 3)}
+                "p99_ms": round(pct(lat, 0.99), 3), "measured": True}
 
     def run_served(arr_s):
         srv = T.tmfg_serve_start(torch.cuda.current_device(), lanes=lanes, max_batch=256,
-                                 mode=MODE, prefix=1)
+                                 mode=MODE, prefix=1, pipeline=True, precision=PIPE_PRECISION,
+                                 lane_bytes=24 << 30)
         res = {}
         base = now() + 2_000_000
-        for i, S in enumerate(mats):
+        for i in range(nreq):
             if arr_s is not None:
                 t_arr = base + int(arr_s[i] * 1e9)
                 while now() < t_arr:
@@ -702,7 +820,7 @@ def run_serving(T, ctx, nreq, stream, lanes=3):
                     d = t_arr - now()
                     if d > 200_000:
                         time.sleep(min(d - 100_000, 1_000_000) / 1e9)
-            T.tmfg_serve_submit(srv, S, out=served_out[i], stream=stream)
+            T.tmfg_serve_submit_pipeline(srv, Xs[i], ks[i], out=served_out[i], stream=stream)
         while len(res) < nreq:
             for r in T.tmfg_serve_poll(srv, 1024, 10000):
                 res[r["id"]] = r
@@ -720,20 +838,35 @@ def run_serving(T, ctx, nreq, stream, lanes=3):
     rates = []
     for load in (0.8, 1.5):
         arr = poisson_arrivals(6000 + int(load * 10), nreq, load * cap)
-        rates.append({"load_vs_plain_capacity": load, "offered_per_s": round(load * cap, 1),
-                      "served": run_served(arr), "plain": run_plain(arr)})
+        entry = {"load_vs_plain_capacity": load, "offered_per_s": round(load * cap, 1),
+                 "served": run_served(arr)}
+        if load < 1.0:
+            entry["plain"] = run_plain(arr)
+        else:
+            lat = fifo_replay(arr, service)
+            entry["plain"] = {"solves_per_s": round(nreq / (max(arr[-1] * 1e3, 0) / 1e3 +
+                                                            lat[-1] / 1e3), 1),
+                              "p50_ms": round(pct(lat, 0.5), 3), "p99_ms": round(pct(lat, 0.99), 3),
+                              "measured": False,
+                              "how": "FIFO queue replayed from the measured per-request "
+                                     "service times (the plain path is one server)"}
+        rates.append(entry)
     sat = run_served(None)
     # equal accuracy: the served outputs equal the plain path's, bit for bit
     same = True
-    for i in range(0, nreq, max(1, nreq // 64)):
-        o = outputs(mats[i])
-        plain_one(mats[i], o)
-        same = same and all(torch.equal(o[k], served_out[i][k]) for k in o)
-    ns = [int(S.shape[0]) for S in mats]
+    for i in range(0, nreq, max(1, nreq // 128)):
+        same = same and same_results(plain_one(i), served_out[i])
+    ns = [r["n"] for r in reqs]
+    del served_out, plain
+    torch.cuda.empty_cache()
     return {"requests": nreq, "n_range": [min(ns), max(ns)], "n_mean": round(float(np.mean(ns)), 1),
-            "lanes": lanes, "tmfg": "corr-tmfg P=1 + exact APSP",
-            "plain_capacity_solves_per_s": round(cap, 1), "poisson": rates,
-            "saturation": sat, "outputs_identical_sampled": bool(same)}
+            "lanes": lanes,
+            "pipeline": f"similarity ({PIPE_PRECISION}) -> corr-tmfg P=1 -> exact APSP -> DBHT "
+                        "-> labels at k",
+            "plain_capacity_solves_per_s": round(cap, 1),
+            "plain_service_p50_ms": round(pct(service, 0.5), 3),
+            "plain_service_p99_ms": round(pct(service, 0.99), 3),
+            "poisson": rates, "saturation": sat, "outputs_identical_sampled": bool(same)}
 
 
 def host_cpu():

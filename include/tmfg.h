@@ -166,6 +166,13 @@ typedef struct {
                               general loop kernel that every mode runs */
 } tmfg_loop_shape;
 
+/* Stage times (ms from the start of the call, on the device clock) of the
+ * last tmfg_solve_host on this context, after waiting for it: [0] start,
+ * [1] every block of S uploaded, [2] TMFG built, [3..6] the four pieces of
+ * the exact distances downloaded, [7] the approximate distances downloaded;
+ * -1 for a stage the call did not have.  count <= 8 entries are written. */
+int tmfg_solve_host_stages(tmfg_ctx *ctx, float *ms, int32_t count);
+
 /* Set the loop shape that later tmfg_build and tmfg_solve_host calls on this
  * context use (NULL = defaults).  TMFG_EINVAL for an unsupported shape. */
 int tmfg_set_loop_shape(tmfg_ctx *ctx, const tmfg_loop_shape *shape);

@@ -137,6 +137,8 @@ def load_library():
         lib.tmfg_cut_labels.restype = ctypes.c_int
         lib.tmfg_serve_submit_pipeline.argtypes = [P, ctypes.POINTER(_PipelineJob), P]
         lib.tmfg_serve_submit_pipeline.restype = i64
+        lib.tmfg_solve_host_stages.argtypes = [P, P, i32]
+        lib.tmfg_solve_host_stages.restype = ctypes.c_int
         lib.tmfg_set_loop_shape.argtypes = [P, ctypes.POINTER(_LoopShape)]
         lib.tmfg_set_loop_shape.restype = ctypes.c_int
         lib.dbht_cluster.argtypes = [P, P, i64, i64, i32, P, P, P, P, P, i64, P, P]
@@ -433,6 +435,15 @@ def dbht_cluster_detail(ctx: Context, S, t, D, linkage=None, stream=None):
     _check(rc, "dbht_cluster_detail")
     info["direction"] = info["direction"][: max(n - 4, 0)]
     return linkage, info
+
+
+def tmfg_solve_host_stages(ctx: Context) -> dict:
+    """Stage times (ms from its start) of the last tmfg_solve_host on ctx."""
+    buf = (ctypes.c_float * 8)()
+    _check(load_library().tmfg_solve_host_stages(ctx.handle, buf, 8), "tmfg_solve_host_stages")
+    names = ["start", "uploads_done", "tmfg_done", "exact_piece1_down", "exact_piece2_down",
+             "exact_piece3_down", "exact_piece4_down", "approx_down"]
+    return {k: round(float(v), 3) for k, v in zip(names, buf) if v >= 0}
 
 
 def _loop_shape(shape) -> "_LoopShape":

@@ -221,6 +221,17 @@ int ensure_io(tmfg_ctx *c, size_t bytes, cudaStream_t stream)
     return TMFG_OK;
 }
 
+int ensure_stage_events(tmfg_ctx *c)
+{
+    if (!c->tev_ready) {
+        for (cudaEvent_t &e : c->tev)
+            if (cudaEventCreate(&e) != cudaSuccess) return TMFG_ECUDA;
+        c->tev_ready = true;
+    }
+    for (bool &u : c->tev_used) u = false;
+    return TMFG_OK;
+}
+
 int ensure_copy_stream(tmfg_ctx *c)
 {
     if (!c->cstream &&
@@ -288,6 +299,8 @@ void tmfg_destroy(tmfg_ctx *ctx)
     if (ctx->cstream) cudaStreamDestroy(ctx->cstream);
     if (ctx->ev_ready)
         for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    if (ctx->tev_ready)
+        for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -641,7 +654,13 @@ int tmfg_solve_host(tmfg_ctx *ctx, const void *S_host, int64_t n, int64_t ld,
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = ensure_copy_stream(ctx);
     if (rc) return rc;
+    rc = ensure_stage_events(ctx);
+    if (rc) return rc;
     cudaStream_t cs = ctx->cstream;
+    auto mark = [&](int i, cudaStream_t on) {
+        ctx->tev_used[i] = true;
+        return cudaEventRecord(ctx->tev[i], on) != cudaSuccess;
+    };
     // one workspace for every stage (no reallocation between them)
     size_t wb = build_work_bytes(n);
     if (D_exact) wb = wb > apsp_work_bytes((int)n, 0, h) ? wb : apsp_work_bytes((int)n, 0, h);
@@ -674,7 +693,8 @@ int tmfg_solve_host(tmfg_ctx *ctx, const void *S_host, int64_t n, int64_t ld,
     cudaEvent_t *ev = ctx->ev;
     auto fail = [](cudaError_t e) { return e != cudaSuccess; };
     // copies wait for the compute stream's earlier work on these buffers
-    if (fail(cudaEventRecord(ev[0], st)) || fail(cudaStreamWaitEvent(cs, ev[0], 0)))
+    if (fail(cudaEventRecord(ev[0], st)) || fail(cudaStreamWaitEvent(cs, ev[0], 0)) ||
+        mark(0, cs))
         return TMFG_ECUDA;
     BuildWork w = build_carve(ctx->work, n);
     // S in row blocks: each block is sorted as soon as it has arrived
@@ -692,12 +712,14 @@ int tmfg_solve_host(tmfg_ctx *ctx, const void *S_host, int64_t n, int64_t ld,
                             ctx->num_sms, st, (int)r0, (int)r1);
         if (rc) return rc;
     }
+    if (mark(1, cs)) return TMFG_ECUDA;
     if (params->flags & TMFG_CHECK_SYMMETRY) {
         rc = check_symmetry(ctx, dS, n, ld, dtype, st);
         if (rc) return rc;
     }
     rc = launch_build_loop(ctx, w, dS, n, ld, params, d_order, d_edges, d_face, d_parent, st);
     if (rc) return rc;
+    if (mark(2, st)) return TMFG_ECUDA;
     // the TMFG goes back while the distances are computed
     auto out_copy = [&](int e, void *dst, const void *src, size_t bytes) {
         return fail(cudaEventRecord(ev[e], st)) || fail(cudaStreamWaitEvent(cs, ev[e], 0)) ||
@@ -731,14 +753,14 @@ int tmfg_solve_host(tmfg_ctx *ctx, const void *S_host, int64_t n, int64_t ld,
             rc = launch_apsp_exact_rows((int)n, ctx->work, dD, n, (int)s0, (int)s1, ctx->status,
                                         ctx->num_sms, ctx->timeout_ns, st);
             if (rc) return rc;
-            if (d_copy(34 + b, D_exact, dD, s0, s1)) return TMFG_ECUDA;
+            if (d_copy(34 + b, D_exact, dD, s0, s1) || mark(3 + b, cs)) return TMFG_ECUDA;
         }
     }
     if (D_approx) {
         rc = launch_apsp(dS, (int)n, ld, dtype, d_edges, 1, h, rf, dDa, n, ctx->work,
                          ctx->status, ctx->num_sms, ctx->timeout_ns, st);
         if (rc) return rc;
-        if (d_copy(38, D_approx, dDa, 0, n)) return TMFG_ECUDA;
+        if (d_copy(38, D_approx, dDa, 0, n) || mark(7, cs)) return TMFG_ECUDA;
     }
     // the call completes on `stream` once every copy has
     if (fail(cudaEventRecord(ev[39], cs)) || fail(cudaStreamWaitEvent(st, ev[39], 0)))
@@ -763,6 +785,22 @@ int tmfg_sync_status(tmfg_ctx *ctx, void *stream)
         return TMFG_ECUDA;
     if (code && cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess) return TMFG_ECUDA;
     return code;
+}
+
+int tmfg_solve_host_stages(tmfg_ctx *ctx, float *ms, int32_t count)
+{
+    if (!ctx || !ms || count < 0) return TMFG_EINVAL;
+    if (!ctx->tev_ready || !ctx->tev_used[0]) return TMFG_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return TMFG_ECUDA;
+    for (int i = 0; i < count && i < 8; ++i) {
+        ms[i] = -1.0f;
+        if (!ctx->tev_used[i]) continue;
+        if (cudaEventSynchronize(ctx->tev[i]) != cudaSuccess ||
+            cudaEventElapsedTime(&ms[i], ctx->tev[0], ctx->tev[i]) != cudaSuccess)
+            return TMFG_ECUDA;
+    }
+    return TMFG_OK;
 }
 
 int tmfg_set_loop_shape(tmfg_ctx *ctx, const tmfg_loop_shape *shape)

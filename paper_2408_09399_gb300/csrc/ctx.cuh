@@ -26,6 +26,11 @@ struct tmfg_ctx {
     cudaStream_t cstream;
     cudaEvent_t ev[40];
     bool ev_ready;
+    // timing events of the last tmfg_solve_host: start, uploads done, TMFG
+    // done, the four exact-distance pieces downloaded, approximate downloaded
+    cudaEvent_t tev[8];
+    bool tev_ready;
+    bool tev_used[8];
 };
 
 namespace tmfg {

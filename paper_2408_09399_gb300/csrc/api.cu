@@ -301,6 +301,10 @@ void tmfg_destroy(tmfg_ctx *ctx)
         for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     if (ctx->tev_ready)
         for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
+    if (ctx->aux_ready) {
+        for (cudaStream_t a : ctx->aux) cudaStreamDestroy(a);
+        for (cudaEvent_t e : ctx->aux_ev) cudaEventDestroy(e);
+    }
     delete ctx;
 }
 

@@ -31,6 +31,11 @@ struct tmfg_ctx {
     cudaEvent_t tev[8];
     bool tev_ready;
     bool tev_used[8];
+    // tmfg_pipeline_run: streams that run the per-request stages side by
+    // side, and the events that fork them from and join them to the caller's
+    cudaStream_t aux[8];
+    cudaEvent_t aux_ev[9];
+    bool aux_ready;
 };
 
 namespace tmfg {

@@ -39,6 +39,38 @@ __global__ void cut_labels_kernel(const double *__restrict__ Z, int n, int k,
     }
 }
 
+constexpr int kPipeStreams = 8;  // requests whose per-request stages run side by side
+
+int ensure_aux_streams(tmfg_ctx *c)
+{
+    if (c->aux_ready) return TMFG_OK;
+    for (cudaStream_t &a : c->aux)
+        if (cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking) != cudaSuccess) return TMFG_ECUDA;
+    for (cudaEvent_t &e : c->aux_ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return TMFG_ECUDA;
+    c->aux_ready = true;
+    return TMFG_OK;
+}
+
+// The first `k` side streams wait for `st`'s work so far.
+bool fork_aux(tmfg_ctx *c, cudaStream_t st, int k)
+{
+    if (cudaEventRecord(c->aux_ev[kPipeStreams], st) != cudaSuccess) return false;
+    for (int i = 0; i < k; ++i)
+        if (cudaStreamWaitEvent(c->aux[i], c->aux_ev[kPipeStreams], 0) != cudaSuccess) return false;
+    return true;
+}
+
+// `st` waits for the first `k` side streams' work so far.
+bool join_aux(tmfg_ctx *c, cudaStream_t st, int k)
+{
+    for (int i = 0; i < k; ++i)
+        if (cudaEventRecord(c->aux_ev[i], c->aux[i]) != cudaSuccess ||
+            cudaStreamWaitEvent(st, c->aux_ev[i], 0) != cudaSuccess)
+            return false;
+    return true;
+}
+
 size_t pipeline_scratch_bytes(int64_t n, int64_t T, int precision)
 {
     size_t b = sim_work_bytes((int)n, (int)T, precision);
@@ -97,19 +129,28 @@ int tmfg_pipeline_run(tmfg_ctx *ctx, const tmfg_pipeline_job *jobs, int32_t coun
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return TMFG_ECUDA;
+    // the per-request stages of request i run on side stream i mod k, each
+    // stream on its own slice of the workspace
+    const int k = count < kPipeStreams ? count : kPipeStreams;
+    scratch = round256(scratch);
     if (cs != cudaStreamCaptureStatusNone) {
-        if (scratch > ctx->work_bytes) return TMFG_ENOMEM;
+        if (!ctx->aux_ready || (size_t)k * scratch > ctx->work_bytes) return TMFG_ENOMEM;
     } else {
-        const int rc = ensure_work(ctx, scratch, st);
+        int rc = ensure_aux_streams(ctx);
+        if (!rc) rc = ensure_work(ctx, (size_t)k * scratch, st);
         if (rc) return rc;
     }
+    auto slice = [&](int i) { return static_cast<char *>(ctx->work) + (size_t)(i % k) * scratch; };
     // 1. the similarity of each instance's series
+    if (!fork_aux(ctx, st, k)) return TMFG_ECUDA;
     for (int i = 0; i < count; ++i) {
         const tmfg_pipeline_job &J = jobs[i];
         const int rc = launch_similarity(J.X, (int)J.n, (int)J.T, J.ldx, prec, J.S, J.n,
-                                         ctx->work, ctx->status, ctx->timeout_ns, st);
+                                         slice(i), ctx->status, ctx->timeout_ns,
+                                         ctx->aux[i % k]);
         if (rc) return rc;
     }
+    if (!join_aux(ctx, st, k)) return TMFG_ECUDA;
     // 2. the batched TMFG and exact APSP
     std::vector<tmfg_job> bj(count);
     for (int i = 0; i < count; ++i) {
@@ -128,20 +169,23 @@ int tmfg_pipeline_run(tmfg_ctx *ctx, const tmfg_pipeline_job *jobs, int32_t coun
     }
     int rc = tmfg_batch_run(ctx, bj.data(), count, &pp->tmfg, cfg, stream);
     if (rc) return rc;
-    // 3. each dendrogram, then its cut
+    // 3. each dendrogram, then its cut (the batch's tables in the workspace
+    // are done with once the batched stages have run: the side streams wait)
+    if (!fork_aux(ctx, st, k)) return TMFG_ECUDA;
     for (int i = 0; i < count; ++i) {
         const tmfg_pipeline_job &J = jobs[i];
+        cudaStream_t as = ctx->aux[i % k];
         rc = launch_dbht(J.S, (int)J.n, J.n, TMFG_F32, J.order, J.edges, J.ins_face,
                          J.bubble_parent, J.D, J.n, J.Z, nullptr, nullptr, nullptr, nullptr,
-                         ctx->work, ctx->status, ctx->num_sms, st);
+                         slice(i), ctx->status, ctx->num_sms, as);
         if (rc) return rc;
         if (J.k > 0) {
-            cut_labels_kernel<<<1, 32, 0, st>>>(J.Z, (int)J.n, J.k, J.labels,
-                                                static_cast<int *>(ctx->work), ctx->status);
+            cut_labels_kernel<<<1, 32, 0, as>>>(J.Z, (int)J.n, J.k, J.labels,
+                                                reinterpret_cast<int *>(slice(i)), ctx->status);
             if (cudaGetLastError() != cudaSuccess) return TMFG_ECUDA;
         }
     }
-    return TMFG_OK;
+    return join_aux(ctx, st, k) ? TMFG_OK : TMFG_ECUDA;
 }
 
 }  // extern "C"

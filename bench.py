@@ -209,7 +209,47 @@ def measured_peaks():
 # DRAM bytes of one full-size corr-tmfg P=1 build of the loop kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum over its 6 segments, from one
 # one-pass ncu capture of the current kernel at n = 20000)
-LOOP_DRAM_BYTES_N20000 = 407_908_864
+LOOP_DRAM_BYTES_N20000 = 407_908_864  # the general loop kernel's build at n = 20000
+
+LOOP_KERNELS = {1: "tmfg_corr1_kernel", 2: "tmfg_loop_kernel", 3: "tmfg_cluster_kernel"}
+
+
+def loop_kernel_of(shape, n):
+    """Name of the loop kernel a shape runs (kernel 0 = the library's own
+    choice: the general kernel where its shared memory holds n)."""
+    k = int((shape or {}).get("kernel", 0))
+    if k == 0:
+        k = 2 if n <= 21575 else 1
+    name = LOOP_KERNELS[k]
+    if k == 3:
+        name += f" (cluster of {int(shape.get('cluster', 8))} CTAs)"
+    return k, name
+
+
+def loop_stats_named(stats, kernel, n):
+    """The 16 loop counters of tmfg_last_stats under the names the kernel
+    that ran gives them (the cluster kernel reuses the slots)."""
+    if kernel != 3:
+        return {**{k: v for k, v in stats.items() if k not in (
+            "cycles_extract", "cycles_validate", "cycles_resolve", "cycles_stale_scan",
+            "epoch_iters")},
+            "pointer_probes": stats["cycles_extract"],
+            "warp_refreshes": stats["cycles_validate"],
+            "warp_refresh_steps": stats["cycles_resolve"]}
+    ins = max(n - 4, 1)
+    per = lambda key: round(stats[key] / ins, 1)  # noqa: E731
+    return {"face_evals": stats["face_evals"], "rounds": stats["rounds"],
+            "loop_ns": stats["loop_ns"], "cluster_ctas": stats["cycles_stale_scan"],
+            "rows_refreshed": stats["cycles_extract"],
+            "rows_past_first_step": stats["cycles_validate"],
+            "row_steps_past_first": stats["cycles_resolve"],
+            "stale_reads_waited": stats["epoch_iters"],
+            "local_refreshes_after_wait": stats["cycles_refresh"],
+            "cycles_per_insertion_cta0": {
+                "A_read_slots": per("stale_pops"), "B_insert_and_scans": per("cycles_recompute"),
+                "C_row_refresh": per("cycles_push"), "D_face_eval": per("cycles_gains"),
+                "E_group_maxima": per("cycles_index"),
+                "F_push_and_cluster_barrier": per("cycles_select")}}
 
 
 def measured_bf16_tflops():
@@ -419,12 +459,13 @@ def run_ours(args, rank, world, local):
         return {"achieved": round(gbs, 1), "frac": round(gbs / hbm_peak, 4),
                 "algorithmic_bytes": int(bytes_), "ms": round(ms, 3)}
 
+    lk, lk_name = loop_kernel_of(loop_tune.get("loop"), n)
     roofline = {"bound": "hbm",
-                "kernel": "tmfg_loop_kernel (the 6 segments of one build, with the 5 row "
-                          "compactions between them)",
+                "kernel": f"{lk_name}: the 6 segments of one build, with the 5 row "
+                          "compactions between them",
                 "achieved": round(loop_gbs, 2), "peak": hbm_peak, "peak_kind": peak_kind,
                 "unit": "GB/s", "frac": round(loop_gbs / hbm_peak, 5),
-                "traffic": LOOP_DRAM_BYTES_N20000 if n == 20000 else None,
+                "traffic": LOOP_DRAM_BYTES_N20000 if (n == 20000 and lk == 2) else None,
                 "algorithmic_bytes": int(loop_bytes), "ms": round(loop_ev_ms, 3),
                 "note": "dependent-latency chain of n-4 insertions (ns per insertion in "
                         "loop_ns_per_insertion); no roof binds it",
@@ -432,20 +473,32 @@ def run_ours(args, rank, world, local):
                                   "apsp_exact": line(4.0 * n * n, apsp_ms),
                                   "apsp_approx": line(4.0 * n * n, apsx_ms)}}
     # the loop's own bound: each insertion is a chain of dependent round
-    # trips -- the updated faces' records (L2) -> the probes of the sorted
-    # rows whose best vertex was inserted (DRAM) -> the gathers of S for the
-    # re-evaluated faces (DRAM) -> the reload of the touched index leaves
-    # (L2) -> the next root.  Latencies measured here by pointer chasing.
+    # trips.  One-CTA kernels: the updated faces' records (L2) -> the probes
+    # of the sorted rows whose best vertex was inserted (DRAM) -> the
+    # gathers of S for the re-evaluated faces (DRAM) -> the reload of the
+    # touched index leaves (L2) -> the next root.  Cluster kernel: the probes
+    # (DRAM) -> the owners' stores into the other CTAs -> the gathers (DRAM)
+    # -> the exchange of the CTAs' best pairs (a cluster barrier).  Latencies
+    # measured here by pointer chasing and by the cluster exchange itself.
     if rank == 0:
         l2_ns = T.tmfg_memory_latency(ctx, 16 << 20, hops=20000, warm=(16 << 20) // 128)
         dram_ns = T.tmfg_memory_latency(ctx, 4 << 30, hops=20000)
         ins_ns = stats["loop_ns"] / max(n - 4, 1)
-        floor_ns = 2.0 * l2_ns + 2.0 * dram_ns
-        roofline["latency"] = {"l2_hit_ns": round(l2_ns, 1), "dram_miss_ns": round(dram_ns, 1),
-                               "chain": "2 L2 + 2 DRAM dependent round trips per insertion",
-                               "floor_ns_per_insertion": round(floor_ns, 1),
-                               "achieved_ns_per_insertion": round(ins_ns, 1),
-                               "frac": round(floor_ns / ins_ns, 4)}
+        lat = {"l2_hit_ns": round(l2_ns, 1), "dram_miss_ns": round(dram_ns, 1)}
+        if lk == 3:
+            cl = int(loop_tune["loop"].get("cluster", 8))
+            ex_ns = T.tmfg_cluster_exchange_latency(ctx, cl, 20000)
+            floor_ns = 2.0 * dram_ns + ex_ns
+            lat.update({"cluster_exchange_ns": round(ex_ns, 1),
+                        "chain": "2 DRAM dependent round trips + 1 cluster exchange per "
+                                 "insertion"})
+        else:
+            floor_ns = 2.0 * l2_ns + 2.0 * dram_ns
+            lat["chain"] = "2 L2 + 2 DRAM dependent round trips per insertion"
+        lat.update({"floor_ns_per_insertion": round(floor_ns, 1),
+                    "achieved_ns_per_insertion": round(ins_ns, 1),
+                    "frac": round(floor_ns / ins_ns, 4)})
+        roofline["latency"] = lat
 
     # e2e: the same step through the host-memory entry point (tmfg_solve_host):
     # S from page-locked host memory, the TMFG and both distance matrices
@@ -508,12 +561,8 @@ def run_ours(args, rank, world, local):
         "config": bench_config(n, world),
         "phases": {k: round(v, 3) for k, v in phases.items()},
         "loop_ns_per_insertion": round(stats["loop_ns"] / max(1, n - 4), 1),
-        "loop_stats": {**{k: v for k, v in stats.items() if k not in (
-            "cycles_extract", "cycles_validate", "cycles_resolve", "cycles_stale_scan",
-            "epoch_iters")},
-            "pointer_probes": stats["cycles_extract"],
-            "warp_refreshes": stats["cycles_validate"],
-            "warp_refresh_steps": stats["cycles_resolve"]},
+        "loop_kernel": lk_name,
+        "loop_stats": loop_stats_named(stats, lk, n),
         "tmfg_variants": alt,
         "loop_autotune": loop_tune,
         "dbht": dbht,

@@ -156,14 +156,19 @@ typedef struct {
 typedef struct {
     int32_t threads;       /* threads of the loop's CTA: 256 (default) or 512 */
     int32_t probe_lanes;   /* lanes per sorted-row refresh: 4, 8 (default) or 16;
-                              with 512 threads 8 or 16 */
+                              with 512 threads 8 or 16; the cluster kernel:
+                              8, 16 or 32 (default) */
     int32_t stage_groups;  /* index groups of 32 face keys a round copies to
                               shared memory (default 128; fewer if they do not fit;
                               -1 = none) */
     int32_t kernel;        /* 0 = automatic (default: the general loop kernel
                               where its shared memory holds n, else the prefix-1
                               kernel), 1 = the prefix-1 loop kernel, 2 = the
-                              general loop kernel that every mode runs */
+                              general loop kernel that every mode runs, 3 = the
+                              cluster kernel (one build on a thread-block
+                              cluster of `cluster` SMs; single builds only:
+                              TMFG_EINVAL in a batch) */
+    int32_t cluster;       /* CTAs (SMs) of the cluster kernel: 8 (default) or 16 */
 } tmfg_loop_shape;
 
 /* Stage times (ms from the start of the call, on the device clock) of the
@@ -491,6 +496,16 @@ int tmfg_last_stats(tmfg_ctx *ctx, int64_t *out, int count);
  * TMFG_ENOMEM (the buffer does not fit) or TMFG_ECUDA on failure. */
 int tmfg_memory_latency(tmfg_ctx *ctx, int64_t bytes, int32_t hops, int32_t warm,
                         double *ns_per_hop);
+
+/* Diagnostic (no paper counterpart): nanoseconds per exchange of one
+ * thread-block cluster of `cluster` (8 or 16) CTAs, each exchange being what
+ * the cluster loop kernel does once per insertion -- every CTA stores a
+ * 16-byte record into a slot of every CTA's shared memory, then the cluster
+ * passes a barrier (release / acquire) -- averaged over `iters` exchanges.
+ * Synchronous (waits for the device); allocates 8 bytes of device memory.
+ * TMFG_EINVAL for a bad argument, TMFG_ECUDA if the launch fails. */
+int tmfg_cluster_exchange_latency(tmfg_ctx *ctx, int32_t cluster, int32_t iters,
+                                  double *ns_per_exchange);
 
 /* Static description of a return code. */
 const char *tmfg_strerror(int code);

@@ -49,7 +49,8 @@ class _Job(ctypes.Structure):
 
 class _LoopShape(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("probe_lanes", ctypes.c_int32),
-                ("stage_groups", ctypes.c_int32), ("kernel", ctypes.c_int32)]
+                ("stage_groups", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("cluster", ctypes.c_int32)]
 
 
 class _BatchConfig(ctypes.Structure):
@@ -172,6 +173,8 @@ def load_library():
         lib.tmfg_last_stats.restype = ctypes.c_int
         lib.tmfg_memory_latency.argtypes = [P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P]
         lib.tmfg_memory_latency.restype = ctypes.c_int
+        lib.tmfg_cluster_exchange_latency.argtypes = [P, ctypes.c_int32, ctypes.c_int32, P]
+        lib.tmfg_cluster_exchange_latency.restype = ctypes.c_int
         lib.tmfg_strerror.argtypes = [ctypes.c_int]
         lib.tmfg_strerror.restype = ctypes.c_char_p
         _lib = lib
@@ -449,15 +452,16 @@ def tmfg_solve_host_stages(ctx: Context) -> dict:
 def _loop_shape(shape) -> "_LoopShape":
     shape = shape or {}
     return _LoopShape(int(shape.get("threads", 0)), int(shape.get("probe_lanes", 0)),
-                      int(shape.get("stage_groups", 0)), int(shape.get("kernel", 0)))
+                      int(shape.get("stage_groups", 0)), int(shape.get("kernel", 0)),
+                      int(shape.get("cluster", 0)))
 
 
 def tmfg_set_loop_shape(ctx: Context, shape=None) -> None:
     """Shape of the corr-tmfg prefix-1 insertion loop for this context's later
     builds: a dict with threads (256/512), probe_lanes (4/8/16),
-    stage_groups (0 default, -1 none) and kernel (0 automatic, 1 the prefix-1
-    kernel, 2 the general one); None restores the defaults.  Every shape
-    gives the same TMFG."""
+    stage_groups (0 default, -1 none), kernel (0 automatic, 1 the prefix-1
+    kernel, 2 the general one, 3 the cluster kernel) and cluster (8 or 16
+    CTAs); None restores the defaults.  Every shape gives the same TMFG."""
     _check(load_library().tmfg_set_loop_shape(ctx.handle, ctypes.byref(_loop_shape(shape))),
            "tmfg_set_loop_shape")
 
@@ -719,6 +723,18 @@ def tmfg_memory_latency(ctx: Context, nbytes: int, hops: int = 20000, warm: int 
     ns = ctypes.c_double()
     _check(load_library().tmfg_memory_latency(ctx.handle, int(nbytes), int(hops), int(warm),
                                               ctypes.byref(ns)), "tmfg_memory_latency")
+    return ns.value
+
+
+def tmfg_cluster_exchange_latency(ctx: Context, cluster: int = 8, iters: int = 20000) -> float:
+    """Nanoseconds per exchange of a cluster of ``cluster`` CTAs: every CTA
+    stores a 16-byte record into every CTA's shared memory, then a cluster
+    barrier (the per-insertion step of the cluster loop kernel; see
+    tmfg_cluster_exchange_latency in include/tmfg.h)."""
+    ns = ctypes.c_double()
+    _check(load_library().tmfg_cluster_exchange_latency(ctx.handle, int(cluster), int(iters),
+                                                        ctypes.byref(ns)),
+           "tmfg_cluster_exchange_latency")
     return ns.value
 
 

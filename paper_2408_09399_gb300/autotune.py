@@ -3,9 +3,10 @@
 Times the shapes a run can take on a sample of the actual work (CUDA
 events, median of a few repeats) and keeps the fastest; every shape gives
 the same results, so only the time decides:
-  - loop: the corr-tmfg prefix-1 insertion loop's kernel (the general one
-    or the prefix-1 one), its threads per CTA, lanes per sorted-row refresh
-    and copied index groups (tmfg_loop_shape);
+  - loop: the corr-tmfg prefix-1 insertion loop's kernel (the general one,
+    the prefix-1 one, or for single builds the cluster one), its threads per
+    CTA, lanes per sorted-row refresh, copied index groups and cluster size
+    (tmfg_loop_shape);
   - sssp_threads: threads per search CTA (256 or 512);
   - chunk: instances per batched launch (a run over more instances than
     this is split into several launches; 2^30 means all at once).
@@ -30,6 +31,11 @@ LOOP_SHAPES = (
     {"kernel": 1, "threads": 256, "probe_lanes": 16},
     {"kernel": 1, "threads": 512, "probe_lanes": 16},
     {"kernel": 1, "threads": 256, "probe_lanes": 8, "stage_groups": -1},
+)
+# single builds may also run on a thread-block cluster (not in batches)
+SINGLE_LOOP_SHAPES = LOOP_SHAPES + (
+    {"kernel": 3, "cluster": 8},
+    {"kernel": 3, "cluster": 16},
 )
 
 
@@ -156,7 +162,7 @@ def tune_loop(ctx, S, mode: str = "corr", prefix: int = 1, repeats: int = 2,
     best = _cached(key, cache_path)
     if not best:
         tried = []
-        for sh in LOOP_SHAPES:
+        for sh in SINGLE_LOOP_SHAPES:
             T.tmfg_set_loop_shape(ctx, sh)
 
             def run():

@@ -386,6 +386,7 @@ int tmfg_batch_run(tmfg_ctx *ctx, const tmfg_job *jobs, int32_t count, const tmf
     if (sssp_threads != 256 && sssp_threads != 512) return TMFG_EINVAL;
     LoopShape shape;
     if (!loop_shape_from(cfg ? &cfg->loop : nullptr, &shape)) return TMFG_EINVAL;
+    if (shape.general == 2) return TMFG_EINVAL;  // the cluster kernel runs single builds only
     const int64_t maxn_lib = tmfg_max_n_mode(dtype, params->mode, params->prefix);
     int max_n = 0, napsp = 0;
     for (int i = 0; i < count; ++i) {

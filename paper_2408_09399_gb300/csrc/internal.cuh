@@ -65,8 +65,10 @@ struct LoopShape {
     int groups = 128;
     // which kernel runs corr-tmfg prefix 1: -1 automatic (the general kernel
     // where its shared memory holds n, else the prefix-1 kernel), 0 the
-    // prefix-1 kernel, 1 the general kernel
+    // prefix-1 kernel, 1 the general kernel, 2 the cluster kernel
     int general = -1;
+    int cluster = 8;          // CTAs of the cluster kernel: 8 or 16
+    int cluster_lanes = 32;   // its lanes per row refresh: 8, 16 or 32
 };
 // LoopShape from the ABI's tmfg_loop_shape (NULL or 0 fields: defaults);
 // false for an unsupported shape
@@ -93,6 +95,12 @@ int launch_corr1(const LoopArgs &a, const LoopShape &shape, int dtype, size_t sm
 int64_t loop_max_n(int dtype, int mode, int prefix);
 int launch_corr1_batch(const LoopArgs *d_args, int count, const LoopShape &shape, int dtype,
                        size_t smem, cudaStream_t stream);
+
+// loop_cluster.cu: corr-tmfg prefix 1 on a cluster of C CTAs (single builds)
+size_t cluster_smem_bytes(int n, int dtype, int C);
+// C CTAs (8 or 16), lanes per row refresh (8, 16 or 32)
+bool cluster_shape_ok(int C, int lanes);
+int launch_cluster_loop(const LoopArgs &a, int dtype, int C, int lanes, cudaStream_t stream);
 
 // apsp.cu
 struct SsspArgs {

@@ -1246,10 +1246,17 @@ bool loop_shape_from(const tmfg_loop_shape *in, LoopShape *out)
         if (in->probe_lanes) s.lanes = in->probe_lanes;
         if (in->stage_groups > 0) s.groups = in->stage_groups;
         if (in->stage_groups < 0) s.groups = 0;
-        if (in->kernel < 0 || in->kernel > 2) return false;
+        if (in->kernel < 0 || in->kernel > 3) return false;
         s.general = in->kernel - 1;
+        if (in->cluster) s.cluster = in->cluster;
+        if (s.general == 2) {
+            // the cluster kernel's lanes per row refresh (default 32)
+            s.cluster_lanes = in->probe_lanes ? in->probe_lanes : 32;
+            s.lanes = 8;
+        }
     }
-    if (!corr1_shape_ok(s.threads, s.lanes)) return false;
+    if (!corr1_shape_ok(s.threads, s.lanes) || !cluster_shape_ok(s.cluster, s.cluster_lanes))
+        return false;
     *out = s;
     return true;
 }
@@ -1275,7 +1282,11 @@ int launch_loop(const LoopArgs &args, int dtype, cudaStream_t stream, const Loop
     if (2 * (size_t)args.n - 4 > 65535) return TMFG_ETOOBIG;
     const bool p1 = args.mode == TMFG_CORR && args.P == 1;
     const size_t gen_smem = loop_smem_bytes(args.n, dtype, args.mode);
-    const bool corr1 = p1 && (shape.general == 0 || (shape.general < 0 && gen_smem > kSmemLimit));
+    const bool clus = p1 && shape.general == 2;
+    if (clus && (!args.state || cluster_smem_bytes(args.n, dtype, shape.cluster) > kSmemLimit))
+        return TMFG_ETOOBIG;
+    const bool corr1 = p1 && !clus &&
+                       (shape.general == 0 || (shape.general < 0 && gen_smem > kSmemLimit));
     const bool heap = args.mode == TMFG_HEAP;
     auto kf = heap ? tmfg_loop_kernel<float, true> : tmfg_loop_kernel<float, false>;
     auto kd = heap ? tmfg_loop_kernel<double, true> : tmfg_loop_kernel<double, false>;
@@ -1290,6 +1301,8 @@ int launch_loop(const LoopArgs &args, int dtype, cudaStream_t stream, const Loop
             if (g < 0) return TMFG_ETOOBIG;
         }
         smem = corr1_smem_bytes(args.n, dtype, g, gp);
+    } else if (clus) {
+        smem = 0;
     } else {
         smem = gen_smem;
         if (smem > kSmemLimit) return TMFG_ETOOBIG;
@@ -1316,7 +1329,10 @@ int launch_loop(const LoopArgs &args, int dtype, cudaStream_t stream, const Loop
         LoopArgs a = args;
         a.k_stop = stops[i];
         a.resume = i > 0;
-        if (corr1) {
+        if (clus) {
+            const int rc = launch_cluster_loop(a, dtype, shape.cluster, shape.cluster_lanes, stream);
+            if (rc) return rc;
+        } else if (corr1) {
             const int rc = launch_corr1(a, shape, dtype, smem, gp, stream);
             if (rc) return rc;
         } else if (dtype == TMFG_F32) {
@@ -1336,6 +1352,7 @@ int launch_loop_batch(const LoopArgs *d_args, int count, int max_n, int dtype, i
                       cudaStream_t stream, const LoopShape &shape)
 {
     if (2 * (size_t)max_n - 4 > 65535) return TMFG_ETOOBIG;
+    if (shape.general == 2) return TMFG_EINVAL;  // the cluster kernel runs single builds only
     const size_t smem = loop_smem_bytes(max_n, dtype, mode);
     if (mode == TMFG_CORR && P == 1 &&
         (shape.general == 0 || (shape.general < 0 && smem > kSmemLimit))) {

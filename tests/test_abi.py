@@ -70,6 +70,8 @@ def test_argument_errors_need_no_device(lib):
     lib.tmfg_memory_latency.argtypes = [P, i64, ctypes.c_int32, ctypes.c_int32, P]
     ns = ctypes.c_double()
     assert lib.tmfg_memory_latency(None, 1 << 20, 10, 0, ctypes.byref(ns)) == 1
+    lib.tmfg_cluster_exchange_latency.argtypes = [P, ctypes.c_int32, ctypes.c_int32, P]
+    assert lib.tmfg_cluster_exchange_latency(None, 8, 10, ctypes.byref(ns)) == 1
 
 
 def test_package_fails_loudly_without_a_device():

@@ -1,6 +1,7 @@
-"""The memory-latency diagnostic (pointer chasing) behind the loop's latency
-bound: an L2-resident chain must be faster than a cold multi-gigabyte one,
-and both must fall in a physically sensible range."""
+"""The latency diagnostics behind the loop's latency bound: an L2-resident
+pointer chain must be faster than a cold multi-gigabyte one, both in a
+physically sensible range, and a cluster exchange (stores into every CTA's
+shared memory, then a cluster barrier) must take between 50 ns and 20 us."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -34,5 +35,18 @@ def test_bad_arguments(T):
         for args in ((100, 10, 0), (1 << 20, 0, 0), (1 << 20, 10, -1)):
             with pytest.raises(T.TmfgError):
                 T.tmfg_memory_latency(ctx, *args)
+    finally:
+        ctx.close()
+
+
+def test_cluster_exchange_latency(T):
+    ctx = T.tmfg_create(0)
+    try:
+        for c in (8, 16):
+            ns = T.tmfg_cluster_exchange_latency(ctx, c, iters=2000)
+            assert 50.0 < ns < 20000.0, (c, ns)
+        for c, it in ((4, 10), (8, 0)):
+            with pytest.raises(T.TmfgError):
+                T.tmfg_cluster_exchange_latency(ctx, c, iters=it)
     finally:
         ctx.close()

@@ -216,13 +216,18 @@ LOOP_KERNELS = {1: "tmfg_corr1_kernel", 2: "tmfg_loop_kernel", 3: "tmfg_cluster_
 
 def loop_kernel_of(shape, n):
     """Name of the loop kernel a shape runs (kernel 0 = the library's own
-    choice: the general kernel where its shared memory holds n)."""
-    k = int((shape or {}).get("kernel", 0))
+    choice: the cluster kernel of 16 CTAs from n = 256 on)."""
+    shape = dict(shape or {})
+    k = int(shape.get("kernel", 0))
     if k == 0:
-        k = 2 if n <= 21575 else 1
+        if n >= 256:
+            k, shape = 3, {"cluster": 16, "probe_lanes": 32}
+        else:
+            k = 2
     name = LOOP_KERNELS[k]
     if k == 3:
-        name += f" (cluster of {int(shape.get('cluster', 8))} CTAs)"
+        name += (f" (cluster of {int(shape.get('cluster') or 8)} CTAs, "
+                 f"{int(shape.get('probe_lanes') or 32)} lanes per row refresh)")
     return k, name
 
 
@@ -486,7 +491,7 @@ def run_ours(args, rank, world, local):
         ins_ns = stats["loop_ns"] / max(n - 4, 1)
         lat = {"l2_hit_ns": round(l2_ns, 1), "dram_miss_ns": round(dram_ns, 1)}
         if lk == 3:
-            cl = int(loop_tune["loop"].get("cluster", 8))
+            cl = int((loop_tune.get("loop") or {}).get("cluster") or 16)
             ex_ns = T.tmfg_cluster_exchange_latency(ctx, cl, 20000)
             floor_ns = 2.0 * dram_ns + ex_ns
             lat.update({"cluster_exchange_ns": round(ex_ns, 1),

@@ -34,8 +34,9 @@ LOOP_SHAPES = (
 )
 # single builds may also run on a thread-block cluster (not in batches)
 SINGLE_LOOP_SHAPES = LOOP_SHAPES + (
-    {"kernel": 3, "cluster": 8},
-    {"kernel": 3, "cluster": 16},
+    {"kernel": 3, "cluster": 8, "probe_lanes": 32},
+    {"kernel": 3, "cluster": 16, "probe_lanes": 16},
+    {"kernel": 3, "cluster": 16, "probe_lanes": 32},
 )
 
 

@@ -63,9 +63,11 @@ struct LoopShape {
     int threads = 256;
     int lanes = 8;
     int groups = 128;
-    // which kernel runs corr-tmfg prefix 1: -1 automatic (the general kernel
-    // where its shared memory holds n, else the prefix-1 kernel), 0 the
-    // prefix-1 kernel, 1 the general kernel, 2 the cluster kernel
+    // which kernel runs corr-tmfg prefix 1: -1 automatic (single builds from
+    // kClusterAutoMinN on: the cluster kernel where the device can place it;
+    // otherwise the general kernel where its shared memory holds n, else the
+    // prefix-1 kernel), 0 the prefix-1 kernel, 1 the general kernel, 2 the
+    // cluster kernel
     int general = -1;
     int cluster = 8;          // CTAs of the cluster kernel: 8 or 16
     int cluster_lanes = 32;   // its lanes per row refresh: 8, 16 or 32
@@ -101,6 +103,13 @@ size_t cluster_smem_bytes(int n, int dtype, int C);
 // C CTAs (8 or 16), lanes per row refresh (8, 16 or 32)
 bool cluster_shape_ok(int C, int lanes);
 int launch_cluster_loop(const LoopArgs &a, int dtype, int C, int lanes, cudaStream_t stream);
+// whether the device can run the cluster kernel of C CTAs for n
+bool cluster_placeable(int n, int dtype, int C, int lanes);
+// the automatic choice takes the cluster kernel (16 CTAs, a warp per row
+// refresh) from this n on, where it is placeable: measured on GB300 it is at
+// least as fast as the one-CTA kernels from n = 300 on (4.5 vs 5.1 ms at
+// n = 1000, 51 vs 65 ms at 10000, 117 vs 194 ms at 20000)
+constexpr int kClusterAutoMinN = 256;
 
 // apsp.cu
 struct SsspArgs {

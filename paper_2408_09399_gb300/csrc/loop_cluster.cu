@@ -747,37 +747,65 @@ bool cluster_shape_ok(int C, int lanes)
 }
 
 namespace {
+// The launch configuration of one cluster of C CTAs; false if the kernel's
+// attributes cannot be set or the device cannot place such a cluster.
 template <typename T, int C, int PL>
-int go_cluster(const LoopArgs &a, size_t smem, cudaStream_t stream)
+bool cluster_config(size_t smem, cudaStream_t stream, cudaLaunchConfig_t *cfg,
+                    cudaLaunchAttribute *at)
 {
     auto kern = tmfg_cluster_kernel<T, C, PL>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return TMFG_ECUDA;
-    if (C > 8 &&
-        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
-        return TMFG_ECUDA;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(C, 1, 1);
-    cfg.blockDim = dim3(kClThreads, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = stream;
-    cudaLaunchAttribute at[1];
+            cudaSuccess ||
+        (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                      cudaSuccess)) {
+        cudaGetLastError();
+        return false;
+    }
+    *cfg = cudaLaunchConfig_t{};
+    cfg->gridDim = dim3(C, 1, 1);
+    cfg->blockDim = dim3(kClThreads, 1, 1);
+    cfg->dynamicSmemBytes = smem;
+    cfg->stream = stream;
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = C;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg->attrs = at;
+    cfg->numAttrs = 1;
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess || nclusters < 1) {
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, cfg) != cudaSuccess || nclusters < 1) {
         cudaGetLastError();
-        return TMFG_ETOOBIG;
+        return false;
     }
-    if (cudaLaunchKernelEx(&cfg, kern, a) != cudaSuccess) return TMFG_ECUDA;
+    return true;
+}
+
+template <typename T, int C, int PL>
+int go_cluster(const LoopArgs &a, size_t smem, cudaStream_t stream)
+{
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute at[1];
+    if (!cluster_config<T, C, PL>(smem, stream, &cfg, at)) return TMFG_ETOOBIG;
+    if (cudaLaunchKernelEx(&cfg, tmfg_cluster_kernel<T, C, PL>, a) != cudaSuccess)
+        return TMFG_ECUDA;
     return TMFG_OK;
 }
 }  // namespace
+
+bool cluster_placeable(int n, int dtype, int C, int lanes)
+{
+    if (!cluster_shape_ok(C, lanes)) return false;
+    const size_t smem = cluster_smem_bytes(n, dtype, C);
+    if (smem > kSmemLimit) return false;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute at[1];
+    // the placement does not depend on the lanes (same threads and memory)
+    if (dtype == TMFG_F32)
+        return C == 16 ? cluster_config<float, 16, 32>(smem, 0, &cfg, at)
+                       : cluster_config<float, 8, 32>(smem, 0, &cfg, at);
+    return C == 16 ? cluster_config<double, 16, 32>(smem, 0, &cfg, at)
+                   : cluster_config<double, 8, 32>(smem, 0, &cfg, at);
+}
 
 namespace {
 template <typename T, int C>

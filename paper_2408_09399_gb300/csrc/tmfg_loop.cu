@@ -1277,10 +1277,17 @@ int64_t loop_max_n(int dtype, int mode, int prefix)
     return m;
 }
 
-int launch_loop(const LoopArgs &args, int dtype, cudaStream_t stream, const LoopShape &shape)
+int launch_loop(const LoopArgs &args, int dtype, cudaStream_t stream, const LoopShape &shape_in)
 {
     if (2 * (size_t)args.n - 4 > 65535) return TMFG_ETOOBIG;
     const bool p1 = args.mode == TMFG_CORR && args.P == 1;
+    LoopShape shape = shape_in;
+    if (p1 && shape.general < 0 && args.state && args.n >= kClusterAutoMinN &&
+        cluster_placeable(args.n, dtype, 16, 32)) {
+        shape.general = 2;
+        shape.cluster = 16;
+        shape.cluster_lanes = 32;
+    }
     const size_t gen_smem = loop_smem_bytes(args.n, dtype, args.mode);
     const bool clus = p1 && shape.general == 2;
     if (clus && (!args.state || cluster_smem_bytes(args.n, dtype, shape.cluster) > kSmemLimit))

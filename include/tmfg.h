@@ -279,11 +279,12 @@ typedef struct {
 /* The whole step from HOST memory: S (host, n x n, leading dimension ld)
  * is copied to the device in row blocks, each block's rows sorted as soon as
  * it has arrived (Algorithm 1's sort overlaps the transfer); then the
- * insertion loop; then the exact APSP (into D_exact) and the approximate
- * APSP (into D_approx), each optional (NULL skips it), with leading
- * dimension ldd.  The TMFG (order, edges, ins_face, bubble_parent) and the
- * distances are written to HOST memory, each copied back while the next
- * stage computes (a second, internal stream carries the copies).  Results
+ * insertion loop; then the approximate APSP (into D_approx) and the exact
+ * APSP (into D_exact, in four pieces of sources), each optional (NULL skips
+ * it), with leading dimension ldd.  The TMFG (order, edges, ins_face,
+ * bubble_parent) and the distances are written to HOST memory, each copied
+ * back while the next stage computes (a second, internal stream carries the
+ * copies).  Results
  * are those of tmfg_build and tmfg_apsp.  Asynchronous and ordered on
  * `stream` like every call: the host buffers are complete once the stream
  * has reached the end of the call (tmfg_sync_status).  Host buffers should

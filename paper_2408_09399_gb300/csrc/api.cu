@@ -748,6 +748,14 @@ int tmfg_solve_host(tmfg_ctx *ctx, const void *S_host, int64_t n, int64_t ld,
                                       4 * (size_t)n, (size_t)(r1 - r0), cudaMemcpyDeviceToHost,
                                       cs));
     };
+    // the approximate matrix first: its download (one block, after its
+    // symmetric pass) overlaps the exact searches
+    if (D_approx) {
+        rc = launch_apsp(dS, (int)n, ld, dtype, d_edges, 1, h, rf, dDa, n, ctx->work,
+                         ctx->status, ctx->num_sms, ctx->timeout_ns, st);
+        if (rc) return rc;
+        if (d_copy(38, D_approx, dDa, 0, n) || mark(7, cs)) return TMFG_ECUDA;
+    }
     if (D_exact) {
         // four pieces of sources: each piece's rows go back while the next computes
         rc = launch_apsp_csr(dS, (int)n, ld, dtype, d_edges, ctx->work, ctx->status, st);
@@ -760,12 +768,6 @@ int tmfg_solve_host(tmfg_ctx *ctx, const void *S_host, int64_t n, int64_t ld,
             if (rc) return rc;
             if (d_copy(34 + b, D_exact, dD, s0, s1) || mark(3 + b, cs)) return TMFG_ECUDA;
         }
-    }
-    if (D_approx) {
-        rc = launch_apsp(dS, (int)n, ld, dtype, d_edges, 1, h, rf, dDa, n, ctx->work,
-                         ctx->status, ctx->num_sms, ctx->timeout_ns, st);
-        if (rc) return rc;
-        if (d_copy(38, D_approx, dDa, 0, n) || mark(7, cs)) return TMFG_ECUDA;
     }
     // the call completes on `stream` once every copy has
     if (fail(cudaEventRecord(ev[39], cs)) || fail(cudaStreamWaitEvent(st, ev[39], 0)))

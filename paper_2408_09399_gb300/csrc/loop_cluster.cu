@@ -33,10 +33,11 @@
 //     best pair and its face's record); the best of them is (v, t).
 //  B. the owner of t rewrites it as {v,x,y}; the owners of faces nf, nf+1
 //     write {v,y,z} and {v,x,z}; every CTA scans the Mc of its rows for v
-//     (the rows to refresh) and the stored vertices of its faces for v (the
-//     faces to recompute).                                         -- barrier
-//  C. groups of PL lanes refresh the listed rows (steps of 1, 2, 4 16-byte
-//     loads per lane) and store the new words into every CTA.     -- barrier
+//     (the rows to refresh).                                       -- barrier
+//  C. groups of PL lanes refresh the listed rows (steps of PL x 8 sorted
+//     ids) and store the new words into every CTA; meanwhile the warps with
+//     no row scan the stored vertices of the CTA's faces for v (the faces
+//     to recompute).                                               -- barrier
 //  D. one thread per listed face: the fresh Mc of its three vertices, 9
 //     gathers of S, gain (S[a,u] + S[b,u]) + S[c,u] in the dtype of S, ties
 //     to the smaller u, the best pair's key into its leaf.         -- barrier
@@ -126,6 +127,46 @@ __device__ __forceinline__ uint2 face_record(int p, int q, int s, int bub)
     return make_uint2((uint32_t)p | ((uint32_t)q << 16), (uint32_t)s | ((uint32_t)bub << 16));
 }
 
+// One thread's refresh of a CTA's replica `word` of a sorted row, when the
+// owner's word did not arrive within the poll bound (out of line: the path is
+// rare and its loop would otherwise be copied into every face evaluation).
+// The word is read again first: the owner's store may have landed meanwhile.
+__device__ __noinline__ uint32_t cl_refresh_thread(const uint16_t *row, const uint32_t *ins,
+                                                   uint32_t *word, int n, int cur_v)
+{
+    auto inserted = [&](int u) { return u == cur_v || ((ins[u >> 5] >> (u & 31)) & 1u); };
+    const int mlen = n - 1;
+    const uint32_t w0 = *(volatile const uint32_t *)word;
+    const int m0 = (int)(w0 & 0xFFFFu);
+    if (m0 == kNone16 || !inserted(m0)) return w0;
+    int p = (int)(w0 >> 16) + 1;
+    int fq = mlen, fe = kNone16;
+    while (p < mlen) {
+        const int base = p & ~7;  // base + 8 <= ldi: both multiples of 8, base < n - 1
+        const uint4 c = *reinterpret_cast<const uint4 *>(row + base);
+        const uint32_t wd[4] = {c.x, c.y, c.z, c.w};
+        bool done = false;
+        for (int t = 0; t < 8 && !done; ++t) {
+            const int q = base + t;
+            if (q < p) continue;
+            const int e = (wd[t >> 1] >> (16 * (t & 1))) & 0xFFFF;
+            if (q >= mlen || e >= n) {
+                fq = q < mlen ? q : mlen;
+                done = true;
+            } else if (!inserted(e)) {
+                fq = q;
+                fe = e;
+                done = true;
+            }
+        }
+        if (done) break;
+        p = base + 8;
+    }
+    const uint32_t nw = ((uint32_t)fq << 16) | (uint32_t)fe;
+    atomicMax(word, nw);
+    return nw;
+}
+
 template <typename T, int C, int PL>
 struct ClLoop {
     using KO = KeyOps<T>;
@@ -157,38 +198,37 @@ struct ClLoop {
     __device__ bool stale(uint32_t w) const { return mc_of(w) != kNone16 && inserted(mc_of(w)); }
     __device__ uint32_t word_at(int w) const { return *(volatile const uint32_t *)(pm + w); }
 
+    // The entries of one 16-byte load (8 ids) equal to v, as bits 0..7.
+    __device__ static uint32_t match8(const uint4 &q, uint32_t vv)
+    {
+        const uint32_t m0 = __vcmpeq2(q.x, vv), m1 = __vcmpeq2(q.y, vv);
+        const uint32_t m2 = __vcmpeq2(q.z, vv), m3 = __vcmpeq2(q.w, vv);
+        return (m0 & 1u) | ((m0 >> 15) & 2u) | ((m1 & 1u) << 2) | ((m1 >> 13) & 8u) |
+               ((m2 & 1u) << 4) | ((m2 >> 11) & 32u) | ((m3 & 1u) << 6) | ((m3 >> 9) & 128u);
+    }
+
     // Every index i < count of a 16-bit array (16-byte aligned, padded to a
-    // multiple of 8 entries) whose entry is v: on_hit(i), by the 256 threads
-    // of the CTA.  Eight entries per 16-byte load, four loads in flight per
-    // thread; a word holds a match when one of its halves of word ^ vv is
-    // zero.
+    // multiple of 8 entries) whose entry is v: on_hit(i), by `stride` threads
+    // (g = this thread's index among them).  Two 16-byte loads (16 entries)
+    // in flight per thread; the matches become one bit mask, handled by a
+    // single copy of on_hit (the loop runs once per insertion, so its code
+    // size is what it costs).
     template <class F>
-    __device__ __forceinline__ void scan_eq(const uint16_t *arr, int count, int v, F on_hit)
+    __device__ __forceinline__ void scan_eq(const uint16_t *arr, int count, int v, int g,
+                                            int stride, F on_hit)
     {
         const uint32_t vv = (uint32_t)v | ((uint32_t)v << 16);
         const uint4 *a8 = reinterpret_cast<const uint4 *>(arr);
         const int nq = (count + 7) >> 3;
-        for (int i0 = threadIdx.x; i0 < nq; i0 += 4 * NT) {
-            uint4 q[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int i = i0 + u * NT;
-                q[u] = i < nq ? a8[i] : make_uint4(~vv, ~vv, ~vv, ~vv);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const uint32_t wd[4] = {q[u].x ^ vv, q[u].y ^ vv, q[u].z ^ vv, q[u].w ^ vv};
-                uint32_t any = 0;
-#pragma unroll
-                for (int h = 0; h < 4; ++h) any |= (wd[h] - 0x00010001u) & ~wd[h] & 0x80008000u;
-                if (!any) continue;
-#pragma unroll
-                for (int h = 0; h < 4; ++h)
-#pragma unroll
-                    for (int b = 0; b < 2; ++b) {
-                        const int e = 8 * (i0 + u * NT) + 2 * h + b;
-                        if (e < count && ((wd[h] >> (16 * b)) & 0xFFFFu) == 0) on_hit(e);
-                    }
+        for (int i0 = g; i0 < nq; i0 += 2 * stride) {
+            const uint4 q0 = a8[i0];
+            const uint4 q1 = i0 + stride < nq ? a8[i0 + stride] : make_uint4(~vv, ~vv, ~vv, ~vv);
+            uint32_t hits = match8(q0, vv) | (match8(q1, vv) << 8);
+            while (hits) {
+                const int j = __ffs(hits) - 1;
+                hits &= hits - 1;
+                const int e = 8 * (j < 8 ? i0 : i0 + stride) + (j & 7);
+                if (e < count) on_hit(e);
             }
         }
     }
@@ -202,7 +242,7 @@ struct ClLoop {
     }
 
     // The owner's refresh of row w by the PL lanes of this lane's
-    // group: from ptr + 1, steps of 1, 2, then 4 16-byte loads per lane,
+    // group: from ptr + 1, steps of one 16-byte load (8 sorted ids) per lane,
     // until the first uninserted id or the end of the row (an id >= n or
     // position n - 1); the new word goes to this CTA's Mc list and to every
     // CTA's replica (lane sl stores into CTAs sl, sl + PL, ...).
@@ -214,32 +254,24 @@ struct ClLoop {
         const uint16_t *row = a.idx + (long long)w * a.ldi;
         int p = ptr_of(pm[w]) + 1;
         int fq = mlen, fe = kNone16;
-        int span = 1, steps = 0;
+        int steps = 0;
         while (p < mlen) {
             const int base = p & ~7;
-            uint4 c[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int q0 = base + (u * PL + sl) * 8;
-                c[u] = (u < span && q0 < a.ldi)
-                           ? *reinterpret_cast<const uint4 *>(row + q0)
-                           : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-            }
+            const int q0 = base + sl * 8;
+            const uint4 c = q0 < a.ldi ? *reinterpret_cast<const uint4 *>(row + q0)
+                                       : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu,
+                                                    0xFFFFFFFFu);
             ++steps;
+            const uint32_t wd[4] = {c.x, c.y, c.z, c.w};
             int best = 0x7FFFFFFF, bid = kNone16;
 #pragma unroll
-            for (int u = 3; u >= 0; --u) {
-                if (u >= span) continue;
-                const uint32_t wd[4] = {c[u].x, c[u].y, c[u].z, c[u].w};
-#pragma unroll
-                for (int t = 7; t >= 0; --t) {
-                    const int q = base + (u * PL + sl) * 8 + t;
-                    const int e = (wd[t >> 1] >> (16 * (t & 1))) & 0xFFFF;
-                    const bool stop = q >= mlen || e >= n;
-                    if (q >= p && (stop || !inserted(e))) {
-                        best = q;
-                        bid = stop ? kNone16 : e;
-                    }
+            for (int t = 7; t >= 0; --t) {
+                const int q = q0 + t;
+                const int e = (wd[t >> 1] >> (16 * (t & 1))) & 0xFFFF;
+                const bool stop = q >= mlen || e >= n;
+                if (q >= p && (stop || !inserted(e))) {
+                    best = q;
+                    bid = stop ? kNone16 : e;
                 }
             }
             int m = best;
@@ -251,8 +283,7 @@ struct ClLoop {
                 fq = m;
                 break;
             }
-            p = base + span * PL * 8;
-            if (span < 4) span <<= 1;
+            p = base + PL * 8;
         }
         const uint32_t word = (fe != kNone16 && fq < mlen)
                                   ? ((uint32_t)fq << 16) | (uint32_t)fe
@@ -272,44 +303,6 @@ struct ClLoop {
         }
     }
 
-    // One thread's refresh of this CTA's replica of row w, when the
-    // owner's word did not arrive within the poll bound.  The word is read
-    // again first: the owner's store may have landed meanwhile.
-    __device__ uint32_t refresh_thread(int w)
-    {
-        const int mlen = n - 1;
-        const uint16_t *row = a.idx + (long long)w * a.ldi;
-        const uint32_t w0 = word_at(w);
-        if (!stale(w0)) return w0;
-        int p = ptr_of(w0) + 1;
-        int fq = mlen, fe = kNone16;
-        while (p < mlen) {
-            const int base = p & ~7;  // base + 8 <= ldi: both multiples of 8, base < n - 1
-            const uint4 c = *reinterpret_cast<const uint4 *>(row + base);
-            const uint32_t wd[4] = {c.x, c.y, c.z, c.w};
-            bool done = false;
-            for (int t = 0; t < 8 && !done; ++t) {
-                const int q = base + t;
-                if (q < p) continue;
-                const int e = (wd[t >> 1] >> (16 * (t & 1))) & 0xFFFF;
-                if (q >= mlen || e >= n) {
-                    fq = q < mlen ? q : mlen;
-                    done = true;
-                } else if (!inserted(e)) {
-                    fq = q;
-                    fe = e;
-                    done = true;
-                }
-            }
-            if (done) break;
-            p = base + 8;
-        }
-        const uint32_t word = ((uint32_t)fq << 16) | (uint32_t)fe;
-        atomicMax(pm + w, word);
-        ++c_slow;
-        return word;
-    }
-
     // The fresh word of vertex w of a face: at once if this CTA's
     // replica is fresh, else after the owner's store arrives (bounded poll),
     // else by a local refresh.
@@ -322,7 +315,8 @@ struct ClLoop {
             x = word_at(w);
             if (!stale(x)) return x;
         }
-        return refresh_thread(w);
+        ++c_slow;
+        return cl_refresh_thread(a.idx + (long long)w * a.ldi, ins, pm + w, n, cur_v);
     }
 
     __device__ void mark_group(int g)
@@ -367,13 +361,25 @@ struct ClLoop {
     __device__ void list_face(int lf) { flist[atomicAdd(fcount, 1)] = (uint16_t)lf; }
 
     // C, D, E of an insertion over the listed rows and faces (the caller has
-    // just passed the barrier after B).  Ends with a barrier.
-    __device__ void round(long long &cyc_ref, long long &cyc_eval, long long &cyc_l1)
+    // just passed the barrier after the row scan).  The warps that no row
+    // refresh needs run face_scan(g, stride) meanwhile (all warps after
+    // their refreshes when every warp has one).  Ends with a barrier.
+    template <class FS>
+    __device__ void round(long long &cyc_ref, long long &cyc_eval, long long &cyc_l1,
+                          FS face_scan)
     {
         const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
         long long c0 = clock64();
         const int rc = *rcount < NR ? *rcount : NR;
-        for (int i = tid / PL; i < rc; i += NG) refresh_row(rows[i]);
+        const int groups = rc < NG ? rc : NG;         // row groups with a row
+        const int rw = (groups * PL + kWarp - 1) / kWarp;  // the warps they occupy
+        if (warp < rw)
+            for (int i = tid / PL; i < rc; i += NG) refresh_row(rows[i]);
+        if (rw < NW) {
+            if (warp >= rw) face_scan(tid - kWarp * rw, NT - kWarp * rw);
+        } else {
+            face_scan(tid, NT);
+        }
         __syncthreads();
         long long c1 = clock64();
         cyc_ref += c1 - c0;
@@ -572,7 +578,7 @@ __device__ __forceinline__ void cluster_body(const LoopArgs &a)
             }
         }
         __syncthreads();
-        st.round(cyc_ref, cyc_eval, cyc_l1);
+        st.round(cyc_ref, cyc_eval, cyc_l1, [](int, int) {});
     }
     // the first slot exchange
     if (warp == 0) st.push_root(0, 0u);
@@ -632,19 +638,20 @@ __device__ __forceinline__ void cluster_body(const LoopArgs &a)
             a.ins_face[3 * k + 2] = fz;
             a.parent[k + 1] = tb;
         }
-        st.scan_eq(st.mco, L.NR, v, [&](int i) {
+        st.scan_eq(st.mco, L.NR, v, tid, NT, [&](int i) {
             const int w = r + C * i;
             if (w < n && st.is_ins(w)) st.list_row(w);
-        });
-        const int nlcur = r < nf_old ? (nf_old - 1 - r) / C + 1 : 0;
-        st.scan_eq(st.fv, nlcur, v, [&](int lf) {
-            if (!(tr == r && lf == tl)) st.list_face(lf);
         });
         __syncthreads();
         long long c2 = clock64();
         cyc_scan += c2 - c1;
-        // C, D, E
-        st.round(cyc_ref, cyc_eval, cyc_l1);
+        // C (with the face scan on the warps that refresh no row), D, E
+        const int nlcur = r < nf_old ? (nf_old - 1 - r) / C + 1 : 0;
+        st.round(cyc_ref, cyc_eval, cyc_l1, [&](int g, int stride) {
+            st.scan_eq(st.fv, nlcur, v, g, stride, [&](int lf) {
+                if (!(tr == r && lf == tl)) st.list_face(lf);
+            });
+        });
         long long c3 = clock64();
         ++k;
         ++rounds;

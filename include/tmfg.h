@@ -169,8 +169,9 @@ typedef struct {
                               loop kernel, 2 = the
                               general loop kernel that every mode runs, 3 = the
                               cluster kernel (one build on a thread-block
-                              cluster of `cluster` SMs; single builds only:
-                              TMFG_EINVAL in a batch) */
+                              cluster of `cluster` SMs; single builds with
+                              n <= 32770 only: TMFG_EINVAL in a batch,
+                              TMFG_ETOOBIG above that n) */
     int32_t cluster;       /* CTAs (SMs) of the cluster kernel: 8 (default) or 16 */
 } tmfg_loop_shape;
 

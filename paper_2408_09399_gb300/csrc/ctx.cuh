@@ -33,8 +33,8 @@ struct tmfg_ctx {
     bool tev_used[8];
     // tmfg_pipeline_run: streams that run the per-request stages side by
     // side, and the events that fork them from and join them to the caller's
-    cudaStream_t aux[8];
-    cudaEvent_t aux_ev[9];
+    cudaStream_t aux[32];
+    cudaEvent_t aux_ev[33];
     bool aux_ready;
 };
 

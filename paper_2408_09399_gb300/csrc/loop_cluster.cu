@@ -65,13 +65,14 @@ namespace tmfg {
 constexpr int kClThreads = 256;
 constexpr int kClWaitPolls = 1 << 16;  // polls of a stale word before refreshing it locally
 
+// One CTA's best pair and its face record, stored into every CTA with one
+// 16-byte store (float keys; two for double keys).  The bubble takes 15 bits
+// (n <= 32770).
 template <class Key>
-struct ClSlot {
-    Key key;        // the CTA's best pair (empty: none)
-    uint32_t xy;    // its face's vertices x | y << 16 (x < y < z)
-    uint32_t zb;    // z | creating bubble << 16
-    uint32_t flag;  // 1: time limit passed (CTA 0)
-    uint32_t pad;
+struct alignas(16) ClSlot {
+    Key key;      // the CTA's best pair (empty: none)
+    uint32_t xy;  // its face's vertices x | y << 16 (x < y < z)
+    uint32_t zb;  // z | creating bubble << 16 | time limit passed (CTA 0) << 31
 };
 
 struct ClLayout {
@@ -81,7 +82,7 @@ struct ClLayout {
 };
 
 // Shared-memory layout of one CTA (dynamic part), computed identically on the
-// host.  ks = key bytes; a slot is ks + 16 bytes.
+// host.  ks = key bytes; a slot is 16 bytes (float keys) or 32 (double).
 __host__ __device__ inline ClLayout cl_layout(int n, int C, size_t ks)
 {
     ClLayout L;
@@ -106,7 +107,7 @@ __host__ __device__ inline ClLayout cl_layout(int n, int C, size_t ks)
     L.off_q1 = o;    o = align16(o + 2 * (size_t)L.G1L);
     L.off_flist = o; o = align16(o + 2 * (size_t)L.NL8);
     L.off_rows = o;  o = align16(o + 2 * (size_t)L.NR8);  // each own row at most once
-    L.off_slot = o;  o = align16(o + 2 * (size_t)C * (ks + 16));
+    L.off_slot = o;  o = align16(o + 2 * (size_t)C * (ks == 8 ? 16 : 32));
     L.total = o;
     return L;
 }
@@ -173,6 +174,7 @@ struct ClLoop {
     using Key = typename KO::Key;
     static constexpr int NT = kClThreads, NW = NT / kWarp, NG = NT / PL;
     static_assert(PL >= 1 && PL <= 32 && (PL & (PL - 1)) == 0, "PL: a power of two <= 32");
+    static_assert(sizeof(ClSlot<Key>) % 16 == 0, "a slot is whole 16-byte words");
 
     const LoopArgs &a;
     const T *S;
@@ -417,11 +419,15 @@ struct ClLoop {
         uint2 fr = make_uint2(0u, 0u);
         if (!KO::is_empty(x)) fr = frec[KO::face(x) / C];
         if (lane < C) {
-            ClSlot<Key> *dst = cg::this_cluster().map_shared_rank(slot + par * C + r, lane);
-            dst->key = x;
-            dst->xy = fr.x;
-            dst->zb = fr.y;
-            dst->flag = flag;
+            ClSlot<Key> val;
+            val.key = x;
+            val.xy = fr.x;
+            val.zb = fr.y | (flag << 31);
+            const uint4 *src = reinterpret_cast<const uint4 *>(&val);
+            uint4 *dst = reinterpret_cast<uint4 *>(
+                cg::this_cluster().map_shared_rank(slot + par * C + r, lane));
+#pragma unroll
+            for (int i = 0; i < (int)(sizeof(val) / 16); ++i) dst[i] = src[i];
         }
     }
 };
@@ -595,12 +601,12 @@ __device__ __forceinline__ void cluster_body(const LoopArgs &a)
         // the best of the C slots (every warp alike)
         const ClSlot<Key> *sl = st.slot + par * C;
         const Key x = lane < C ? sl[lane].key : KO::empty();
-        const uint32_t fl = lane < C ? sl[lane].flag : 0u;
+        const uint32_t fl = lane < C ? sl[lane].zb >> 31 : 0u;
         const Key best = warp_max<KO>(x);
         const uint32_t flags = __reduce_or_sync(0xffffffffu, fl);
         const unsigned who = __ballot_sync(0xffffffffu, lane < C && L_::same(x, best));
         const int wr = who ? __ffs(who) - 1 : 0;
-        const uint32_t xy = sl[wr].xy, zb = sl[wr].zb;
+        const uint32_t xy = sl[wr].xy, zb = sl[wr].zb & 0x7FFFFFFFu;
         const int nf_old = 4 + 2 * k;
         const int v = KO::is_empty(best) ? -1 : KO::vert(best);
         const int t = KO::is_empty(best) ? -1 : KO::face(best);
@@ -744,6 +750,8 @@ __global__ void __launch_bounds__(kClThreads, 1) tmfg_cluster_kernel(LoopArgs a)
 
 size_t cluster_smem_bytes(int n, int dtype, int C)
 {
+    // a slot keeps the bubble in 15 bits: n - 3 bubbles must fit
+    if (n > 32770) return ~(size_t)0;
     const size_t ks = dtype == TMFG_F32 ? sizeof(unsigned long long) : sizeof(Key128);
     return cl_layout(n, C, ks).total;
 }

@@ -74,3 +74,25 @@ def test_batch_twice_reuses_staging(T, ctx):
     T.tmfg_sync_status(ctx)
     for x, y in zip(a, reversed(b)):
         assert torch.equal(x["edges"], y["edges"]) and torch.equal(x["D"], y["D"])
+
+
+
+@pytest.mark.parametrize("threads", [256, 512])
+def test_batch_search_shapes_equal_single_and_oracle(T, ctx, threads):
+    """Both CTA sizes of the batched exact search give tmfg_apsp's distances,
+    which equal the oracle's float path sums: ragged sizes from 4 to 4096,
+    ties from quantized S."""
+    ns = [4, 5, 33, 250, 1100, 4096] + sizes(11, 6, 6, 900)
+    mats_np = [W.random_similarity(700 + i, n, np.float32, "quantized" if i % 2 else "uniform")
+               for i, n in enumerate(ns)]
+    mats = [torch.as_tensor(S, device="cuda:0") for S in mats_np]
+    outs = T.tmfg_batch_run(ctx, mats, "corr", 1, apsp=True, sssp_threads=threads)
+    T.tmfg_sync_status(ctx)
+    for S_np, S, o in zip(mats_np, mats, outs):
+        n = S.shape[0]
+        D1 = T.tmfg_apsp(ctx, S, o["edges"])
+        T.tmfg_sync_status(ctx)
+        assert torch.equal(o["D"], D1), (n, threads)
+        if n <= 300:
+            ref = oracle.apsp_exact(S_np, o["edges"].cpu().numpy(), prec=32)
+            assert np.array_equal(o["D"].cpu().numpy().astype(np.float64), ref), (n, threads)

@@ -330,17 +330,33 @@ struct ClLoop {
     // Best pair of local face lf from the fresh Mc of its
     // vertices: 9 independent gathers; gain (S[a,u] + S[b,u]) + S[c,u]
     // round-to-nearest in the dtype of S; ties to the smaller u.  The key
-    // (with the global face id) goes to the face's leaf.
+    // (with the global face id) goes to the face's leaf.  The gathers of the
+    // vertices whose replica word is already fresh are issued before the
+    // wait for the others.
     __device__ void eval_face(int lf)
     {
         const uint2 fr = frec[lf];
         const int xs[3] = {(int)(fr.x & 0xFFFFu), (int)(fr.x >> 16), (int)(fr.y & 0xFFFFu)};
         int cs[3];
+        bool st[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) cs[i] = mc_of(fresh_word(xs[i]));
+        for (int i = 0; i < 3; ++i) {
+            const uint32_t w = word_at(xs[i]);
+            st[i] = stale(w);
+            cs[i] = mc_of(w);
+        }
         T v[3][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
+            if (st[i]) continue;
+            const int col = cs[i] < n ? cs[i] : 0;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) v[i][j] = S[(long long)xs[j] * a.ld + col];
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (!st[i]) continue;
+            cs[i] = mc_of(fresh_word(xs[i]));
             const int col = cs[i] < n ? cs[i] : 0;
 #pragma unroll
             for (int j = 0; j < 3; ++j) v[i][j] = S[(long long)xs[j] * a.ld + col];

@@ -265,24 +265,31 @@ struct ClLoop {
                                                     0xFFFFFFFFu);
             ++steps;
             const uint32_t wd[4] = {c.x, c.y, c.z, c.w};
-            int best = 0x7FFFFFFF, bid = kNone16;
+            // bit t: position q0 + t ends the scan (at or after p; the row's
+            // end or an uninserted id)
+            uint32_t um = 0;
 #pragma unroll
-            for (int t = 7; t >= 0; --t) {
+            for (int t = 0; t < 8; ++t) {
                 const int q = q0 + t;
                 const int e = (wd[t >> 1] >> (16 * (t & 1))) & 0xFFFF;
                 const bool stop = q >= mlen || e >= n;
-                if (q >= p && (stop || !inserted(e))) {
-                    best = q;
-                    bid = stop ? kNone16 : e;
-                }
+                const int ec = stop ? 0 : e;
+                const bool ins_e = ec == cur_v || ((ins[ec >> 5] >> (ec & 31)) & 1u);
+                um |= (uint32_t)(q >= p && (stop || !ins_e)) << t;
             }
-            int m = best;
-#pragma unroll
-            for (int o = PL / 2; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(gmask, m, o));
-            if (m != 0x7FFFFFFF) {
-                const unsigned who = __ballot_sync(gmask, best == m) & gmask;
-                fe = __shfl_sync(gmask, bid, __ffs(who) - 1);
-                fq = m;
+            // lanes hold consecutive runs of 8: the lowest lane with a bit
+            // holds the first such position
+            const unsigned hit = __ballot_sync(gmask, um != 0u) & gmask;
+            if (hit) {
+                const int t = um ? __ffs(um) - 1 : 0;
+                const uint32_t sel = t < 2 ? c.x : t < 4 ? c.y : t < 6 ? c.z : c.w;
+                const int e = (int)((sel >> (16 * (t & 1))) & 0xFFFFu);
+                const int q = q0 + t;
+                const bool stop = q >= mlen || e >= n;
+                const uint32_t pk = ((uint32_t)q << 16) | (uint32_t)(stop ? kNone16 : e);
+                const uint32_t got = __shfl_sync(gmask, pk, __ffs(hit) - 1);
+                fq = (int)(got >> 16);
+                fe = (int)(got & 0xFFFFu);
                 break;
             }
             p = base + PL * 8;

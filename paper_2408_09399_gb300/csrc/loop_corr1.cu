@@ -212,31 +212,46 @@ struct Corr1 {
                            : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
             }
             ++steps;
-            // this lane's first candidate position (ids from the loads in
-            // position order: chunk u of every lane precedes chunk u + 1)
-            int best = 0x7FFFFFFF, bid = kNone16;
+            // bit t of um[u]: position base + (u * PL + sl) * 8 + t ends the
+            // scan (at or after p; the row's end or an uninserted id)
+            uint32_t um[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-            for (int u = 3; u >= 0; --u) {
+            for (int u = 0; u < 4; ++u) {
                 if (u >= span) continue;
                 const uint32_t wd[4] = {c[u].x, c[u].y, c[u].z, c[u].w};
 #pragma unroll
-                for (int t = 7; t >= 0; --t) {
+                for (int t = 0; t < 8; ++t) {
                     const int q = base + (u * PL + sl) * 8 + t;
                     const int e = (wd[t >> 1] >> (16 * (t & 1))) & 0xFFFF;
                     const bool stop = q >= mlen || e >= n;
-                    if (q >= p && (stop || !is_ins(e))) {
-                        best = q;
-                        bid = stop ? kNone16 : e;
-                    }
+                    um[u] |= (uint32_t)(q >= p && (stop || !is_ins(stop ? 0 : e))) << t;
                 }
             }
-            int m = best;
+            // positions run chunk by chunk (chunk u of every lane before
+            // chunk u + 1), lane by lane within a chunk: the first chunk with
+            // a bit, its lowest lane with one, that lane's lowest bit
+            int hu = -1;
+            unsigned hit = 0u;
 #pragma unroll
-            for (int o = PL / 2; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(gmask, m, o));
-            if (m != 0x7FFFFFFF) {
-                const unsigned who = __ballot_sync(gmask, best == m) & gmask;
-                fe = __shfl_sync(gmask, bid, __ffs(who) - 1);
-                fq = m;
+            for (int u = 0; u < 4; ++u) {
+                const unsigned h = __ballot_sync(gmask, um[u] != 0u) & gmask;
+                if (hu < 0 && h) {
+                    hu = u;
+                    hit = h;
+                }
+            }
+            if (hu >= 0) {
+                const uint32_t mk = hu == 0 ? um[0] : hu == 1 ? um[1] : hu == 2 ? um[2] : um[3];
+                const uint4 ch = hu == 0 ? c[0] : hu == 1 ? c[1] : hu == 2 ? c[2] : c[3];
+                const int t = mk ? __ffs(mk) - 1 : 0;
+                const uint32_t sel = t < 2 ? ch.x : t < 4 ? ch.y : t < 6 ? ch.z : ch.w;
+                const int e = (int)((sel >> (16 * (t & 1))) & 0xFFFFu);
+                const int q = base + (hu * PL + sl) * 8 + t;
+                const bool stop = q >= mlen || e >= n;
+                const uint32_t pk = ((uint32_t)q << 16) | (uint32_t)(stop ? kNone16 : e);
+                const uint32_t got = __shfl_sync(gmask, pk, __ffs(hit) - 1);
+                fq = (int)(got >> 16);
+                fe = (int)(got & 0xFFFFu);
                 break;
             }
             p = base + span * PL * 8;

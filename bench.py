@@ -215,15 +215,16 @@ LOOP_KERNELS = {1: "tmfg_corr1_kernel", 2: "tmfg_loop_kernel", 3: "tmfg_cluster_
 
 
 def loop_kernel_of(shape, n):
-    """Name of the loop kernel a shape runs (kernel 0 = the library's own
-    choice: the cluster kernel of 16 CTAs from n = 256 on)."""
+    """Name of the loop kernel a corr-tmfg prefix-1 build with this shape
+    runs (kernel 0 = the library's own choice: the cluster kernel of 16 CTAs
+    from n = 256 on, else the prefix-1 kernel)."""
     shape = dict(shape or {})
     k = int(shape.get("kernel", 0))
     if k == 0:
         if n >= 256:
             k, shape = 3, {"cluster": 16, "probe_lanes": 32}
         else:
-            k = 2
+            k = 1
     name = LOOP_KERNELS[k]
     if k == 3:
         name += (f" (cluster of {int(shape.get('cluster') or 8)} CTAs, "

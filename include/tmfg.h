@@ -161,11 +161,11 @@ typedef struct {
     int32_t stage_groups;  /* index groups of 32 face keys a round copies to
                               shared memory (default 128; fewer if they do not fit;
                               -1 = none) */
-    int32_t kernel;        /* 0 = automatic (default: single builds with n >= 256
-                              take the cluster kernel with 16 CTAs and 32 lanes
-                              where the device can place it; otherwise the
-                              general loop kernel where its shared memory holds
-                              n, else the prefix-1 kernel), 1 = the prefix-1
+    int32_t kernel;        /* 0 = automatic (default: corr-tmfg with prefix 1
+                              takes the cluster kernel with 16 CTAs and 32 lanes
+                              in single builds with n >= 256 where the device
+                              can place it, else the prefix-1 kernel; every
+                              other mode the general kernel), 1 = the prefix-1
                               loop kernel, 2 = the
                               general loop kernel that every mode runs, 3 = the
                               cluster kernel (one build on a thread-block

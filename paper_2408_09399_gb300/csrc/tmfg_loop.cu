@@ -1307,8 +1307,9 @@ int launch_loop(const LoopArgs &args, int dtype, cudaStream_t stream, const Loop
     const bool clus = p1 && shape.general == 2;
     if (clus && (!args.state || cluster_smem_bytes(args.n, dtype, shape.cluster) > kSmemLimit))
         return TMFG_ETOOBIG;
-    const bool corr1 = p1 && !clus &&
-                       (shape.general == 0 || (shape.general < 0 && gen_smem > kSmemLimit));
+    // corr-tmfg with prefix 1 off the cluster kernel: the prefix-1 kernel
+    // unless the general one is asked for
+    const bool corr1 = p1 && !clus && shape.general <= 0;
     const bool heap = args.mode == TMFG_HEAP;
     auto kf = heap ? tmfg_loop_kernel<float, true> : tmfg_loop_kernel<float, false>;
     auto kd = heap ? tmfg_loop_kernel<double, true> : tmfg_loop_kernel<double, false>;
@@ -1376,8 +1377,9 @@ int launch_loop_batch(const LoopArgs *d_args, int count, int max_n, int dtype, i
     if (2 * (size_t)max_n - 4 > 65535) return TMFG_ETOOBIG;
     if (shape.general == 2) return TMFG_EINVAL;  // the cluster kernel runs single builds only
     const size_t smem = loop_smem_bytes(max_n, dtype, mode);
-    if (mode == TMFG_CORR && P == 1 &&
-        (shape.general == 0 || (shape.general < 0 && smem > kSmemLimit))) {
+    // corr-tmfg with prefix 1 runs on the prefix-1 kernel unless the general
+    // one is asked for
+    if (mode == TMFG_CORR && P == 1 && shape.general <= 0) {
         if (!corr1_shape_ok(shape.threads, shape.lanes)) return TMFG_EINVAL;
         // two CTAs per SM when they fit, else one
         int g = corr1_fit_groups(max_n, dtype, shape.groups, kSmemLimit / 2 - 4096, false);

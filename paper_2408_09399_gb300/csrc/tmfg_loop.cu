@@ -151,14 +151,11 @@ struct Loop {
                 e[0] = c.x & 0xFFFF; e[1] = c.x >> 16; e[2] = c.y & 0xFFFF; e[3] = c.y >> 16;
                 e[4] = c.z & 0xFFFF; e[5] = c.z >> 16; e[6] = c.w & 0xFFFF; e[7] = c.w >> 16;
             }
-            uint32_t um = 0;  // bit t: position q0 + t ends the scan
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
+            for (int t = 7; t >= 0; --t) {
                 const int q = q0 + t;
-                const bool stop = q >= mlen || e[t] >= n;
-                um |= (uint32_t)(q >= p && (stop || !is_ins(stop ? 0 : e[t]))) << t;
+                if (q >= p && (q >= mlen || e[t] >= n || !is_ins(e[t]))) first = t;
             }
-            if (um) first = __ffs(um) - 1;
             if (lane == 0) {
                 ++n_scan;
                 ++n_wsteps;
@@ -217,31 +214,21 @@ struct Loop {
                                         : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
         ++n_scan;
         ++n_probes;
-        // all 64 checks independent (their shared-memory reads overlap) and
-        // gathered as bits; the first candidate wins
-        uint32_t m0 = 0, m1 = 0;
+        // all 64 checks independent (their shared-memory reads overlap); the
+        // first candidate wins
+        int first = 64, hit = kNone16;
 #pragma unroll
-        for (int j = 0; j < 64; ++j) {
+        for (int j = 63; j >= 0; --j) {
             const uint4 &cc = c[j >> 3];
             const uint32_t wd = ((j >> 1) & 3) == 0 ? cc.x : ((j >> 1) & 3) == 1 ? cc.y
                               : ((j >> 1) & 3) == 2 ? cc.z : cc.w;
             const int e = (wd >> (16 * (j & 1))) & 0xFFFF;
             const int q = base + j;
             const bool stop = q >= mlen || e >= n;
-            const uint32_t cand = q >= p && (stop || !is_ins(stop ? 0 : e));
-            if (j < 32) m0 |= cand << j;
-            else m1 |= cand << (j - 32);
+            const bool cand = q >= p && (stop || !is_ins(e));
+            if (cand) { first = j; hit = stop ? kNone16 : e; }
         }
-        if (m0 | m1) {
-            const int first = m0 ? __ffs(m0) - 1 : 31 + __ffs(m1);
-            uint4 cc = c[0];
-#pragma unroll
-            for (int h = 1; h < 8; ++h)
-                if ((first >> 3) == h) cc = c[h];
-            const uint32_t wd = ((first >> 1) & 3) == 0 ? cc.x : ((first >> 1) & 3) == 1 ? cc.y
-                              : ((first >> 1) & 3) == 2 ? cc.z : cc.w;
-            const int e = (wd >> (16 * (first & 1))) & 0xFFFF;
-            const int hit = base + first >= mlen || e >= n ? kNone16 : e;
+        if (first < 64) {
             const int q = base + first;
             if (hit != kNone16) {
                 ptr[w] = (uint16_t)q;
@@ -280,14 +267,12 @@ struct Loop {
             e[0] = c.x & 0xFFFF; e[1] = c.x >> 16; e[2] = c.y & 0xFFFF; e[3] = c.y >> 16;
             e[4] = c.z & 0xFFFF; e[5] = c.z >> 16; e[6] = c.w & 0xFFFF; e[7] = c.w >> 16;
         }
-        uint32_t um = 0;  // bit t: position q0 + t ends the scan
+        int first = 8;
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
+        for (int t = 7; t >= 0; --t) {
             const int q = q0 + t;
-            const bool stop = q >= mlen || e[t] >= n;
-            um |= (uint32_t)(q >= p && (stop || !is_ins(stop ? 0 : e[t]))) << t;
+            if (q >= p && (q >= mlen || e[t] >= n || !is_ins(e[t]))) first = t;
         }
-        const int first = um ? __ffs(um) - 1 : 8;
         int hit = kNone16;
 #pragma unroll
         for (int u = 0; u < 8; ++u)
